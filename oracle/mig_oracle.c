@@ -1,0 +1,619 @@
+/*
+ * CPU ORACLE for path-dependent marginal information gain with depth buffers.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. It shares no code with the CUDA library and
+ * includes none of its headers; it is a plain, slow, direct statement of the method:
+ *
+ *   - the depth-buffer method (Sec. IV-A..C), restated step by step over the tree in
+ *     depth order, with the integer readings listed in the design notes (all decisions are
+ *     integer: quantised inputs, exact rational DDA, exact integer projection);
+ *   - the visible-voxel sets I(n, psi) of Eq. 1, and the exact marginal gain of Eq. 2 by a
+ *     depth-first walk with per-voxel reference counts (route 2 of the exact reference; the
+ *     hash-set merge of Sec. I / Sec. IV-E is route 1, in oracle/exact.py).
+ *
+ * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -shared -fPIC (no -ffast-math).
+ * Parity: pinned by the tests in tests/test_oracle_*.py (brute-force DDA with exact
+ * rationals, voxel-centric owner sets, closed-form depth and volume, invariants of Eq. 2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef int64_t i64;
+
+#define ONE_Q16 ((i64)65536)
+#define ONE_Q30 ((i64)1073741824)
+#define OR_UNKNOWN 0
+#define OR_FREE 1
+#define OR_OCCUPIED 2
+#define OR_MAX_DEPTH 64
+
+enum { MODE_MARGINAL = 0, MODE_SINGLE_PARENT = 1, MODE_ABSOLUTE = 2 };
+
+/* Planted mistakes for the pin-strength tests (tests/test_oracle_mutants.py). The default
+ * build defines none; each variant .so is built with -DORACLE_MUTANT=<m> and must fail at
+ * least one pin. MUT(m) is 1 only in variant m. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+#define MUT(m) (ORACLE_MUTANT == (m))
+
+/* floor(a / b) for b > 0, for any sign of a */
+static i64 floor_div(i64 a, i64 b) {
+    i64 q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+static int32_t q30(double x) { return (int32_t)llrint(x * 1073741824.0); }
+static int32_t q16(double x) { return (int32_t)llrint(x * 65536.0); }
+
+/* ------------------------------------------------------------------------------------
+ * Camera model (Eq. 5): pinhole with principal point at the image centre, focal lengths
+ * from the field of view, rays through pixel centres. Camera axes: x right, y down,
+ * z forward; body forward = world +x at yaw 0; pitch positive = nose down; yaw bins
+ * psi_k = 2 pi k / K counter-clockwise about world +z.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    int W, H, K;
+    double t_h, t_v, cp, sp;
+    int32_t *bx, *by, *bz, *dzc; /* per pixel j*W+i: body-frame unit ray (Q30), camera z of it (Q30) */
+    int32_t *ck, *sk;            /* per yaw: cos, sin (Q30) */
+    int32_t *M;                  /* per yaw: rows mu, mv, mz (Q16): (u z, v z, z) = M r */
+} cam_t;
+
+static void cam_free(cam_t *c) {
+    free(c->bx); free(c->by); free(c->bz); free(c->dzc);
+    free(c->ck); free(c->sk); free(c->M);
+}
+
+static int cam_build(cam_t *c, float hfov_deg, float vfov_deg, int W, int H, int K, float pitch_deg) {
+    memset(c, 0, sizeof(*c));
+    if (W < 1 || H < 1 || W > 2048 || H > 2048 || K < 1 || K > 1024) return -1;
+    if (!(hfov_deg > 0.0f && hfov_deg < 180.0f && vfov_deg > 0.0f && vfov_deg < 180.0f)) return -1;
+    if (!(pitch_deg >= -90.0f && pitch_deg <= 90.0f)) return -1;
+    c->W = W; c->H = H; c->K = K;
+    c->t_h = tan(((double)hfov_deg * 0.5) * (M_PI / 180.0));
+    c->t_v = tan(((double)vfov_deg * 0.5) * (M_PI / 180.0));
+    double th = (double)pitch_deg * (M_PI / 180.0);
+    c->cp = cos(th);
+    c->sp = sin(th);
+    size_t np = (size_t)W * H;
+    c->bx = malloc(np * 4); c->by = malloc(np * 4); c->bz = malloc(np * 4); c->dzc = malloc(np * 4);
+    c->ck = malloc((size_t)K * 4); c->sk = malloc((size_t)K * 4); c->M = malloc((size_t)K * 9 * 4);
+    if (!c->bx || !c->by || !c->bz || !c->dzc || !c->ck || !c->sk || !c->M) { cam_free(c); return -2; }
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            /* tangent-plane coordinates of the pixel centre: (i + 1/2 - c_x) / f_x */
+            double a = ((double)(2 * i + (MUT(1) ? 0 : 1) - W) / (double)W) * c->t_h;
+            double b = ((double)(2 * j + 1 - H) / (double)H) * c->t_v;
+            double nrm = sqrt((a * a + b * b) + 1.0);
+            double cx = a / nrm, cy = b / nrm, cz = 1.0 / nrm;
+            size_t p = (size_t)j * W + i;
+            c->bx[p] = q30(cz * c->cp - cy * c->sp);
+            c->by[p] = q30(MUT(2) ? cx : -cx);
+            c->bz[p] = q30(-(cy * c->cp + cz * c->sp));
+            c->dzc[p] = q30(cz);
+        }
+    }
+    double fx = ((double)W * 0.5) / c->t_h, fy = ((double)H * 0.5) / c->t_v;
+    double cxp = (double)W * 0.5, cyp = (double)H * 0.5;
+    for (int k = 0; k < K; ++k) {
+        double ang = ((2.0 * M_PI) * (double)k) / (double)K;
+        double cs = cos(ang), sn = sin(ang);
+        c->ck[k] = q30(cs);
+        c->sk[k] = q30(sn);
+        double ex[3] = {sn, -cs, 0.0};
+        double ey[3] = {-(c->sp * cs), -(c->sp * sn), -c->cp};
+        double ez[3] = {c->cp * cs, c->cp * sn, -c->sp};
+        for (int a = 0; a < 3; ++a) {
+            double mu = fx * ex[a] + cxp * ez[a];
+            double mv = fy * ey[a] + cyp * ez[a];
+            if (fabs(mu) * 65536.0 >= 2147483647.0 || fabs(mv) * 65536.0 >= 2147483647.0) { cam_free(c); return -1; }
+            c->M[k * 9 + a] = q16(mu);
+            c->M[k * 9 + 3 + a] = q16(mv);
+            c->M[k * 9 + 6 + a] = q16(ez[a]);
+        }
+    }
+    return 0;
+}
+
+/* world direction of pixel p at yaw k (Q30): yaw rotation of the body-frame ray */
+static void cam_dir(const cam_t *c, int k, size_t p, i64 d[3]) {
+    i64 bx = c->bx[p], by = c->by[p];
+    d[0] = floor_div((i64)c->ck[k] * bx - (i64)c->sk[k] * by, ONE_Q30);
+    d[1] = floor_div((MUT(12) ? -1 : 1) * (i64)c->sk[k] * bx + (i64)c->ck[k] * by, ONE_Q30);
+    d[2] = c->bz[p];
+}
+
+/* Eq. 5 in integers: project voxel centre v into the camera at P (Q16) with yaw k.
+ * Returns 1 and the pixel when the centre is in front (z > 0); *Zq = z in Q32. */
+static int project(const cam_t *c, int k, const i64 P[3], const int32_t v[3], i64 *pu, i64 *pv, i64 *Zq) {
+    i64 r[3];
+    for (int a = 0; a < 3; ++a) r[a] = (i64)v[a] * ONE_Q16 + ONE_Q16 / 2 - P[a];
+    const int32_t *m = c->M + (size_t)k * 9;
+    i64 U = (i64)m[0] * r[0] + (i64)m[1] * r[1] + (MUT(4) ? 0 : (i64)m[2] * r[2]);
+    i64 V = (i64)m[3] * r[0] + (i64)m[4] * r[1] + (i64)m[5] * r[2];
+    i64 Z = (i64)m[6] * r[0] + (i64)m[7] * r[1] + (i64)m[8] * r[2];
+    *Zq = Z;
+    if (Z <= 0) return 0;
+    *pu = MUT(3) ? U / Z : floor_div(U, Z);
+    *pv = MUT(3) ? V / Z : floor_div(V, Z);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Map
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const uint8_t *g;
+    int n[3];
+} grid_t;
+
+static uint8_t grid_at(const grid_t *G, const int32_t v[3]) {
+    return G->g[((size_t)v[2] * G->n[1] + v[1]) * G->n[0] + v[0]];
+}
+
+/* ------------------------------------------------------------------------------------
+ * 3D DDA (Amanatides-Woo, "Woo 1987", Sec. IV-B) on the quantised ray P + t d.
+ * t is compared as an exact rational n/|d| per axis (n = distance to the next face in
+ * Q16, |d| in Q30); the axis with the smallest next crossing steps, ties x, then y,
+ * then z. A voxel is visited iff its entry t is < T (range); the ray ends on an
+ * occupied voxel (visited, not counted), at the range, or on leaving the grid.
+ * The visitor returns 0 to continue. Returns 1 on an occupied hit and the depth of the
+ * hit's entry point in Q16 voxel units through *D (Sec. IV-A), else 0 and the range
+ * endpoint's depth.
+ * ------------------------------------------------------------------------------------ */
+typedef int (*visit_fn)(void *ctx, const int32_t v[3], uint8_t code);
+
+static int dda(const grid_t *G, const i64 P[3], const i64 d[3], i64 Tq, i64 dzc, visit_fn fn, void *ctx,
+               uint32_t *D) {
+    int32_t v[3];
+    int step[3];
+    i64 nn[3], ad[3];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = (int32_t)floor_div(P[a], ONE_Q16);
+        if (d[a] > 0) { step[a] = 1; ad[a] = d[a]; nn[a] = ((i64)v[a] + 1) * ONE_Q16 - P[a]; }
+        else if (d[a] < 0) { step[a] = -1; ad[a] = -d[a]; nn[a] = P[a] - (i64)v[a] * ONE_Q16; }
+        else { step[a] = 0; ad[a] = 0; nn[a] = ONE_Q16; }
+    }
+    i64 ne = 0, ade = 1; /* entry t of the current voxel = ne / ade (scaled) */
+    for (;;) {
+        uint8_t code = grid_at(G, v);
+        if (fn) fn(ctx, v, code);
+        if (code == OR_OCCUPIED) {
+            if (D) *D = (uint32_t)floor_div((MUT(7) && ade > 1 ? ne + ONE_Q16 : ne) * dzc, ade);
+            return 1;
+        }
+        int best = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (ad[a] == 0) continue;
+            if (best < 0 || (MUT(5) ? nn[a] * ad[best] <= nn[best] * ad[a] : nn[a] * ad[best] < nn[best] * ad[a])) best = a;
+        }
+        /* next entry t = nn[best]/ad[best] (voxel units: nn * 2^14 / ad); stop if >= T */
+        if (MUT(6) ? nn[best] * ONE_Q30 > Tq * ad[best] : nn[best] * ONE_Q30 >= Tq * ad[best]) break;
+        v[best] += step[best];
+        if (v[best] < 0 || v[best] >= G->n[best]) break;
+        ne = nn[best];
+        ade = ad[best];
+        nn[best] += ONE_Q16;
+    }
+    if (D) *D = (uint32_t)floor_div(Tq * dzc, ONE_Q30);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Tree evaluation (Sec. IV-C): levels in increasing depth; per node and yaw, cast all
+ * pixel rays, count owned unknown voxels (absolute, Eq. 1) and those no ancestor's depth
+ * buffer observes (marginal, Eq. 2 by depth buffers, Sec. IV-B); argmax over yaw; keep
+ * the depth buffer of the selected yaw (Sec. IV-A).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const cam_t *cam;
+    const grid_t *G;
+    int k;
+    i64 pi, pj;
+    const i64 *P;
+    int n_anc;
+    const i64 (*anc_P)[3];
+    const int *anc_yaw;
+    uint32_t *const *anc_D;
+    i64 abs_count, marg_count;
+} count_ctx;
+
+static int owned(const cam_t *c, int k, const i64 P[3], const int32_t v[3], i64 pi, i64 pj) {
+    i64 pu, pv, Z;
+    if (!project(c, k, P, v, &pu, &pv, &Z)) return 0;
+    return pu == pi && pv == pj;
+}
+
+static int observed_by(const cam_t *c, const i64 Pa[3], int ka, const uint32_t *Da, const int32_t v[3]) {
+    i64 pu, pv, Z;
+    if (!project(c, ka, Pa, v, &pu, &pv, &Z)) return 0;
+    if (pu < 0 || pu >= c->W || pv < 0 || pv >= c->H) return 0;
+    i64 Dq = Da[(size_t)pv * c->W + (size_t)pu];
+    return MUT(10) ? Z < Dq * ONE_Q16 : Z < (Dq + 1) * ONE_Q16; /* floor(z in Q16) <= stored depth */
+}
+
+static int count_visit(void *vctx, const int32_t v[3], uint8_t code) {
+    count_ctx *x = (count_ctx *)vctx;
+    if (code != OR_UNKNOWN) return 0;
+    if (!MUT(8) && !owned(x->cam, x->k, x->P, v, x->pi, x->pj)) return 0;
+    x->abs_count++;
+    for (int a = 0; a < x->n_anc; ++a)
+        if (observed_by(x->cam, x->anc_P[a], x->anc_yaw[a], x->anc_D[a], v)) return 0;
+    x->marg_count++;
+    return 0;
+}
+
+static int quantize_pos(const float *pos, const float origin[3], float voxel, const int dims[3], i64 P[3]) {
+    for (int a = 0; a < 3; ++a) {
+        double q = (((double)pos[a] - (double)origin[a]) / (double)voxel) * 65536.0;
+        P[a] = llrint(q);
+        if (P[a] < 0 || P[a] >= (i64)dims[a] * ONE_Q16) return -1;
+    }
+    return 0;
+}
+
+static int tree_depths(int n, const int32_t *parent, int32_t *depth) {
+    int roots = 0;
+    for (int i = 0; i < n; ++i) {
+        if (parent[i] == -1) roots++;
+        else if (parent[i] < 0 || parent[i] >= n || parent[i] == i) return -1;
+    }
+    if (n > 0 && roots != 1) return -1;
+    for (int i = 0; i < n; ++i) {
+        int d = 0, p = i;
+        while (parent[p] != -1) {
+            p = parent[p];
+            if (++d > OR_MAX_DEPTH) return -1; /* cycle or too deep */
+        }
+        depth[i] = d;
+    }
+    return 0;
+}
+
+/* Returns 0, or a negative code on invalid input. Outputs per node: absolute gain
+ * max_k abs[n][k], marginal gain marg[n][psi_n], psi_n = lowest k maximising the mode's
+ * gain. Optional: per-(node, yaw) counts and every evaluated node's depth buffer. */
+int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, const float *origin,
+                     int n, const int32_t *parent, const float *pos,
+                     float hfov, float vfov, int W, int H, float range_m, int K, float pitch,
+                     int mode, const uint8_t *node_mask,
+                     int32_t *abs_out, int32_t *marg_out, int32_t *yaw_out,
+                     int32_t *cnt_abs, int32_t *cnt_marg, uint32_t *depth_out, int n_threads) {
+    if (n < 0 || nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return -1;
+    if (!(voxel > 0.0f)) return -1;
+    if (mode < 0 || mode > 2) return -1;
+    if (n == 0) return 0;
+    for (size_t i = 0, m = (size_t)nx * ny * nz; i < m; ++i)
+        if (grid[i] > OR_OCCUPIED) return -1;
+    cam_t cam;
+    int rc = cam_build(&cam, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    i64 Tq = llrint(((double)range_m / (double)voxel) * 65536.0);
+    if (Tq < 1 || Tq > 1024 * ONE_Q16) { cam_free(&cam); return -1; }
+    grid_t G = {grid, {nx, ny, nz}};
+    int dims[3] = {nx, ny, nz};
+    int32_t *depth = malloc((size_t)n * 4);
+    i64 (*P)[3] = malloc((size_t)n * sizeof(*P));
+    int32_t *yaw = malloc((size_t)n * 4);
+    uint32_t **Dn = calloc((size_t)n, sizeof(uint32_t *));
+    int32_t *cabs = malloc((size_t)n * K * 4), *cmarg = malloc((size_t)n * K * 4);
+    if (!depth || !P || !yaw || !Dn || !cabs || !cmarg) { rc = -2; goto done; }
+    if (tree_depths(n, parent, depth)) { rc = -1; goto done; }
+    for (int i = 0; i < n; ++i)
+        if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P[i])) { rc = -1; goto done; }
+    if (node_mask) /* the evaluated subset must be closed under ancestors */
+        for (int i = 0; i < n; ++i)
+            if (node_mask[i] && parent[i] >= 0 && !node_mask[parent[i]]) { rc = -1; goto done; }
+    int max_d = 0;
+    for (int i = 0; i < n; ++i) if (depth[i] > max_d) max_d = depth[i];
+    size_t WH = (size_t)W * H;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    int *lvl = malloc((size_t)n * sizeof(int));
+    if (!lvl) { rc = -2; goto done; }
+    for (int d = 0; d <= max_d && rc == 0; ++d) {
+        int L = 0;
+        for (int i = 0; i < n; ++i)
+            if (depth[i] == d && (!node_mask || node_mask[i])) lvl[L++] = i;
+        /* counts for every (node of the level, yaw) */
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+        for (int li = 0; li < L; ++li) {
+            for (int k = 0; k < K; ++k) {
+                int nd = lvl[li];
+                i64 anc_P[OR_MAX_DEPTH][3];
+                int anc_yaw[OR_MAX_DEPTH];
+                uint32_t *anc_D[OR_MAX_DEPTH];
+                int na = 0;
+                if (mode != MODE_ABSOLUTE) {
+                    for (int p = parent[nd]; p >= 0; p = parent[p]) { /* parent first */
+                        memcpy(anc_P[na], P[p], sizeof(anc_P[na]));
+                        anc_yaw[na] = yaw[p];
+                        anc_D[na] = Dn[p];
+                        na++;
+                        if (mode == MODE_SINGLE_PARENT || MUT(9)) break;
+                    }
+                }
+                count_ctx x = {&cam, &G, k, 0, 0, P[nd], na, (const i64(*)[3])anc_P, anc_yaw, anc_D, 0, 0};
+                for (int j = 0; j < H; ++j) {
+                    for (int i = 0; i < W; ++i) {
+                        size_t p = (size_t)j * W + i;
+                        i64 dvec[3];
+                        cam_dir(&cam, k, p, dvec);
+                        x.pi = i;
+                        x.pj = j;
+                        dda(&G, P[nd], dvec, Tq, cam.dzc[p], count_visit, &x, NULL);
+                    }
+                }
+                cabs[(size_t)nd * K + k] = (int32_t)x.abs_count;
+                cmarg[(size_t)nd * K + k] = (int32_t)x.marg_count;
+            }
+        }
+        /* yaw selection (Sec. III-B): lowest k with the largest gain of the mode */
+        for (int li = 0; li < L; ++li) {
+            int nd = lvl[li];
+            const int32_t *sel = (mode == MODE_ABSOLUTE) ? cabs + (size_t)nd * K : cmarg + (size_t)nd * K;
+            int kb = 0;
+            int32_t amax = cabs[(size_t)nd * K];
+            for (int k = 1; k < K; ++k) {
+                if (MUT(11) ? sel[k] >= sel[kb] : sel[k] > sel[kb]) kb = k;
+                if (cabs[(size_t)nd * K + k] > amax) amax = cabs[(size_t)nd * K + k];
+            }
+            yaw[nd] = kb;
+            abs_out[nd] = amax;
+            marg_out[nd] = cmarg[(size_t)nd * K + kb];
+            yaw_out[nd] = kb;
+            Dn[nd] = malloc(WH * 4);
+            if (!Dn[nd]) rc = -2;
+        }
+        if (rc) break;
+        /* depth buffer of the selected yaw (Sec. IV-A), kept for the descendants */
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+        for (int li = 0; li < L; ++li) {
+            for (int j = 0; j < H; ++j) {
+                int nd = lvl[li];
+                for (int i = 0; i < W; ++i) {
+                    size_t p = (size_t)j * W + i;
+                    i64 dvec[3];
+                    cam_dir(&cam, yaw[nd], p, dvec);
+                    uint32_t Dv = 0;
+                    dda(&G, P[nd], dvec, Tq, cam.dzc[p], NULL, NULL, &Dv);
+                    Dn[nd][p] = Dv;
+                }
+            }
+        }
+    }
+    free(lvl);
+    if (rc == 0) {
+        for (int i = 0; i < n; ++i) {
+            if (node_mask && !node_mask[i]) continue;
+            if (cnt_abs) memcpy(cnt_abs + (size_t)i * K, cabs + (size_t)i * K, (size_t)K * 4);
+            if (cnt_marg) memcpy(cnt_marg + (size_t)i * K, cmarg + (size_t)i * K, (size_t)K * 4);
+            if (depth_out) memcpy(depth_out + (size_t)i * WH, Dn[i], WH * 4);
+        }
+    }
+done:
+    if (Dn) for (int i = 0; i < n; ++i) free(Dn[i]);
+    free(Dn); free(depth); free(P); free(yaw); free(cabs); free(cmarg);
+    cam_free(&cam);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Debug and pin entry points
+ * ------------------------------------------------------------------------------------ */
+
+/* camera tables as the oracle builds them (for pins against a float pinhole model) */
+int oracle_camera_tables(float hfov, float vfov, int W, int H, int K, float pitch,
+                         int32_t *body /* H*W*3 */, int32_t *dzc /* H*W */, int32_t *ck, int32_t *sk,
+                         int32_t *M /* K*9 */, double *tv4 /* t_h, t_v, cp, sp */) {
+    cam_t c;
+    int rc = cam_build(&c, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    size_t np = (size_t)W * H;
+    for (size_t p = 0; p < np; ++p) {
+        body[3 * p] = c.bx[p]; body[3 * p + 1] = c.by[p]; body[3 * p + 2] = c.bz[p];
+        dzc[p] = c.dzc[p];
+    }
+    memcpy(ck, c.ck, (size_t)K * 4);
+    memcpy(sk, c.sk, (size_t)K * 4);
+    memcpy(M, c.M, (size_t)K * 9 * 4);
+    tv4[0] = c.t_h; tv4[1] = c.t_v; tv4[2] = c.cp; tv4[3] = c.sp;
+    cam_free(&c);
+    return 0;
+}
+
+/* world ray directions of every (yaw, pixel): K*H*W*3 int64 (Q30) */
+int oracle_ray_dirs(float hfov, float vfov, int W, int H, int K, float pitch, int64_t *out) {
+    cam_t c;
+    int rc = cam_build(&c, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    for (int k = 0; k < K; ++k)
+        for (size_t p = 0; p < (size_t)W * H; ++p) cam_dir(&c, k, p, out + 3 * ((size_t)k * W * H + p));
+    cam_free(&c);
+    return 0;
+}
+
+typedef struct {
+    int32_t *out;
+    uint8_t *codes;
+    int cap, count;
+} trace_ctx;
+
+static int trace_visit(void *vctx, const int32_t v[3], uint8_t code) {
+    trace_ctx *t = (trace_ctx *)vctx;
+    if (t->count < t->cap) {
+        t->out[3 * t->count] = v[0]; t->out[3 * t->count + 1] = v[1]; t->out[3 * t->count + 2] = v[2];
+        if (t->codes) t->codes[t->count] = code;
+    }
+    t->count++;
+    return 0;
+}
+
+/* One ray: P (Q16), d (Q30), T (Q16), dzc (Q30). Writes up to cap visited voxels; returns
+ * the number visited (may exceed cap), *hit, *D. */
+int oracle_trace(const uint8_t *grid, int nx, int ny, int nz, const int64_t *P, const int64_t *d, int64_t Tq,
+                 int64_t dzc, int cap, int32_t *vox, uint8_t *codes, int32_t *hit, uint32_t *D) {
+    grid_t G = {grid, {nx, ny, nz}};
+    for (int a = 0; a < 3; ++a)
+        if (P[a] < 0 || P[a] >= (i64)G.n[a] * ONE_Q16) return -1;
+    if (d[0] == 0 && d[1] == 0 && d[2] == 0) return -1;
+    trace_ctx t = {vox, codes, cap, 0};
+    uint32_t Dv = 0;
+    *hit = dda(&G, P, d, Tq, dzc, trace_visit, &t, &Dv);
+    *D = Dv;
+    return t.count;
+}
+
+/* Eq. 5 projection of voxel centres (for pins): out = (ok, pu, pv, Zq) per voxel */
+int oracle_project(float hfov, float vfov, int W, int H, int K, float pitch, int k, const int64_t *P, int nv,
+                   const int32_t *vox, int64_t *out) {
+    cam_t c;
+    int rc = cam_build(&c, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    for (int i = 0; i < nv; ++i) {
+        i64 pu = 0, pv = 0, Z = 0;
+        int ok = project(&c, k, P, vox + 3 * (size_t)i, &pu, &pv, &Z);
+        out[4 * (size_t)i] = ok; out[4 * (size_t)i + 1] = pu; out[4 * (size_t)i + 2] = pv; out[4 * (size_t)i + 3] = Z;
+    }
+    cam_free(&c);
+    return 0;
+}
+
+/* the ancestor test of Sec. IV-B for one voxel against one depth buffer (for pins) */
+int oracle_observed(float hfov, float vfov, int W, int H, int K, float pitch, int k, const int64_t *P,
+                    const uint32_t *D, const int32_t *vox) {
+    cam_t c;
+    int rc = cam_build(&c, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    int r = observed_by(&c, P, k, D, vox);
+    cam_free(&c);
+    return r;
+}
+
+int oracle_quantize(const float *pos, int n, const float *origin, float voxel, int nx, int ny, int nz, int64_t *P) {
+    int dims[3] = {nx, ny, nz};
+    for (int i = 0; i < n; ++i)
+        if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P + 3 * (size_t)i)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Exact part (Eq. 1 sets, Eq. 2 by reference counts)
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const cam_t *cam;
+    int k;
+    i64 pi, pj;
+    const i64 *P;
+    int nx, ny;
+    int32_t *ids;
+    i64 count, cap;
+} set_ctx;
+
+static int set_visit(void *vctx, const int32_t v[3], uint8_t code) {
+    set_ctx *s = (set_ctx *)vctx;
+    if (code != OR_UNKNOWN) return 0;
+    if (!owned(s->cam, s->k, s->P, v, s->pi, s->pj)) return 0;
+    if (s->ids && s->count < s->cap) s->ids[s->count] = (int32_t)(((i64)v[2] * s->ny + v[1]) * s->nx + v[0]);
+    s->count++;
+    return 0;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* I(n, yaw[n]) for every node: linear voxel ids (x fastest), sorted. Two calls: with
+ * ids == NULL fills offsets[0..n] (sizes); then with ids of length offsets[n]. */
+int oracle_visible_sets(const uint8_t *grid, int nx, int ny, int nz, float voxel, const float *origin,
+                        int n, const float *pos, const int32_t *yaws,
+                        float hfov, float vfov, int W, int H, float range_m, int K, float pitch,
+                        const uint8_t *node_mask, int64_t *offsets, int32_t *ids, int n_threads) {
+    cam_t cam;
+    int rc = cam_build(&cam, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    i64 Tq = llrint(((double)range_m / (double)voxel) * 65536.0);
+    grid_t G = {grid, {nx, ny, nz}};
+    int dims[3] = {nx, ny, nz};
+    i64 (*P)[3] = malloc((size_t)(n > 0 ? n : 1) * sizeof(*P));
+    for (int i = 0; i < n; ++i)
+        if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P[i])) { free(P); cam_free(&cam); return -1; }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    if (!ids) offsets[0] = 0;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int nd = 0; nd < n; ++nd) {
+        if (node_mask && !node_mask[nd]) { if (!ids) offsets[nd + 1] = 0; continue; }
+        if (yaws[nd] < 0 || yaws[nd] >= K) { bad = 1; continue; }
+        set_ctx s = {&cam, yaws[nd], 0, 0, P[nd], nx, ny, NULL, 0, 0};
+        if (ids) { s.ids = ids + offsets[nd]; s.cap = offsets[nd + 1] - offsets[nd]; }
+        for (int j = 0; j < H; ++j)
+            for (int i = 0; i < W; ++i) {
+                size_t p = (size_t)j * W + i;
+                i64 dvec[3];
+                cam_dir(&cam, yaws[nd], p, dvec);
+                s.pi = i; s.pj = j;
+                dda(&G, P[nd], dvec, Tq, cam.dzc[p], set_visit, &s, NULL);
+            }
+        if (!ids) offsets[nd + 1] = s.count;
+        else qsort(s.ids, (size_t)s.count, 4, cmp_i32);
+    }
+    if (!ids) for (int i = 0; i < n; ++i) offsets[i + 1] += offsets[i];
+    free(P);
+    cam_free(&cam);
+    return bad ? -1 : 0;
+}
+
+/* Route 2 of the exact marginal gain (Eq. 2): depth-first over the tree with a dense
+ * per-voxel reference count of the sets on the current root path. E(n) = number of
+ * voxels of I(n) whose count is zero when n is entered. */
+int oracle_exact_dfs(int n, const int32_t *parent, const int64_t *offsets, const int32_t *ids, int64_t nvox,
+                     const uint8_t *node_mask, int32_t *E) {
+    if (n == 0) return 0;
+    uint16_t *cnt = calloc((size_t)nvox, sizeof(uint16_t));
+    int *head = malloc((size_t)n * sizeof(int)), *next = malloc((size_t)n * sizeof(int));
+    int *stack = malloc((size_t)n * 2 * sizeof(int));
+    if (!cnt || !head || !next || !stack) { free(cnt); free(head); free(next); free(stack); return -2; }
+    int root = -1;
+    for (int i = 0; i < n; ++i) head[i] = -1;
+    for (int i = n - 1; i >= 0; --i) {
+        if (parent[i] < 0) root = i;
+        else { next[i] = head[parent[i]]; head[parent[i]] = i; }
+    }
+    int sp = 0;
+    stack[sp++] = root; /* entries: node (enter) or ~node (leave) */
+    while (sp > 0) {
+        int e = stack[--sp];
+        if (e >= 0) {
+            int nd = e;
+            if (node_mask && !node_mask[nd]) continue;
+            int32_t z = 0;
+            for (i64 q = offsets[nd]; q < offsets[nd + 1]; ++q) if (cnt[ids[q]] == 0 || (MUT(13) && cnt[ids[q]] == 1)) z++;
+            E[nd] = z;
+            for (i64 q = offsets[nd]; q < offsets[nd + 1]; ++q) cnt[ids[q]]++;
+            stack[sp++] = ~nd;
+            for (int c = head[nd]; c >= 0; c = next[c]) stack[sp++] = c;
+        } else {
+            int nd = ~e;
+            for (i64 q = offsets[nd]; q < offsets[nd + 1]; ++q) cnt[ids[q]]--;
+        }
+    }
+    free(cnt); free(head); free(next); free(stack);
+    return 0;
+}

@@ -1,0 +1,52 @@
+"""Pin strength: each planted mistake in the oracle (built as a separate variant with
+-DORACLE_MUTANT=m, on the CPU) must make at least one pin of test_oracle_pins fail.
+The mistakes are the plausible ones: a dropped pixel-centre offset, a mirrored axis,
+truncation instead of floor, a dropped projection term, a reversed DDA tie rule, an
+inclusive range test, exit instead of entry depth, no owner test, parent-only exclusion,
+a strict depth comparison, highest-index yaw ties, a flipped yaw sign, and an exact route
+that double counts."""
+import pytest
+
+import oracle
+import test_oracle_pins as pins  # noqa: E402
+from synth import Sensor
+
+MUTANTS = list(range(1, 14))
+
+PIN_CALLS = [
+    lambda o: pins.test_dda_matches_exact_slab_brute_force(o),
+    lambda o: pins.test_dda_tie_rule_x_then_y_then_z(o),
+    lambda o: pins.test_dda_stops_at_range_and_grid(o),
+    lambda o: pins.test_ray_directions_match_float_pinhole(o, Sensor(87, 58, 48, 28, 5.0, 12, 10.0)),
+    lambda o: pins.test_projection_matches_float_pinhole(o, Sensor(87, 58, 48, 28, 5.0, 12, 10.0)),
+    lambda o: pins.test_depth_of_fronto_parallel_wall(o),
+    lambda o: pins.test_ancestor_test_is_smaller_or_equal(o),
+    lambda o: pins.test_depth_of_range_endpoint(o),
+    lambda o: pins.test_owner_set_equals_voxel_centric_brute_force(o),
+    lambda o: pins.test_absolute_gain_frustum_volume_closed_form(o),
+    lambda o: pins.test_marginal_invariants(o, 1),
+    lambda o: pins.test_fixed_yaw_ordering_abs_sp_all(o),
+    lambda o: pins.test_disjoint_frusta_and_identical_pose(o),
+    lambda o: pins.test_exact_routes_agree_and_telescope(o, 2),
+    lambda o: pins.test_tiny_config_gap_is_small_and_positive(o),
+]
+
+
+@pytest.mark.parametrize("mutant", MUTANTS)
+def test_planted_mistake_fails_a_pin(mutant):
+    o = oracle.load_variant(mutant)
+    o.build()
+    failed = []
+    for i, call in enumerate(PIN_CALLS):
+        try:
+            call(o)
+        except (AssertionError, o.OracleError, RuntimeError):
+            failed.append(i)
+    assert failed, f"mutant {mutant} passed every pin"
+
+
+def test_unmutated_oracle_passes_every_pin():
+    o = oracle
+    o.build()
+    for call in PIN_CALLS:
+        call(o)

@@ -1,0 +1,369 @@
+"""Benchmark: marginal-gain throughput of the GB300 path on the seeded synthetic workloads.
+
+Default (N=1): the paper-scale workload, 400x400x100 voxels at 0.1 m, a 500-node RRT of depth
+<= 10, 160x120 rays, K = 16 yaws, 6 m range. One step = one whole-tree evaluation (every node,
+yaw and ray: count, ancestor test, yaw argmax, depth render).
+  value = marginal-gain rays per second = nodes * K * W * H / device time, inputs resident in HBM,
+          timed with CUDA events on the library's stream, L2 flushed between steps;
+  e2e   = the same metric through the public host-array call (mig_tree_eval), host<->device
+          copies inside the timed region.
+Multi-GPU (torchrun, one rank per GPU): replicas only. Every rank evaluates its own seeded tree
+per step, no collective on the data path; value = all ranks' rays / max-over-ranks time.
+
+--impl reference: the CPU oracle (the plain C restatement of the method) timed on this host's
+cores on a bounded sample of the same workload, same metric and unit.
+--workload batched | serving | large | tiny: the other configurations (batched vs plain, the
+serving loop with p50/p99 latency); see the design doc.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "marginal-gain rays/s & replans/s; p50/p99 replan latency, batched vs plain"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+# ----------------------------------------------------------------------------- utilities
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_flush_buffer(torch, dev):
+    return torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel
+    source (the summary records the source hash); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- workloads
+def make_problem(workload, rank):
+    import synth
+    if workload == "paper_scale":
+        return synth.paper_scale(seed=202 + 1000 * rank)
+    if workload == "tiny":
+        return synth.tiny(seed=101 + 1000 * rank)
+    if workload == "large":
+        return synth.large(seed=303 + 1000 * rank)
+    raise ValueError(workload)
+
+
+WORKLOAD_DESC = {
+    "paper_scale": "paper-scale: 400x400x100 voxels @0.1 m (rooms, 5 prior scans), 500-node RRT depth<=10, "
+                   "160x120 rays, 90x60 deg, 6 m, K=16 yaws",
+    "tiny": "tiny: 64x64x32 @0.2 m, 20-node RRT depth<=4, 36x24 rays, 4 m, K=8",
+    "large": "large: 800x800x200 @0.05 m (Perlin terrain), 2000-node RRT depth<=15, 320x240 rays, 8 m, K=36",
+}
+
+
+def oracle_sample_mask(tree, max_depth_sample):
+    d = tree.depth()
+    return (d <= max_depth_sample).astype(np.uint8)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    import paper_2609_40297_gb300 as mig
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = make_problem(args.workload, rank)
+    s = prob.sensor
+    n = prob.tree.n
+    max_depth = int(prob.tree.depth().max())
+    rays_per_step = n * s.yaw_bins * s.width * s.height
+    ctx = mig.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    m = mig.Map(ctx, prob.map.grid, prob.map.voxel_size, prob.map.origin)
+    par = torch.from_numpy(prob.tree.parent).to(dev)
+    pos = torch.from_numpy(prob.tree.pos).to(dev)
+    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(3)]
+    flush = l2_flush_buffer(torch, dev)
+
+    def step():
+        mig.tree_eval_device(m, par, pos, s, max_depth, *outs)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    # algorithmic work of one step (instrumented pass, untimed)
+    ref_out, stats = mig.tree_eval_stats(m, prob.tree.parent, prob.tree.pos, s)
+    # ---- timed region: K steps, device time per step with CUDA events, L2 flushed between steps
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    ktimes = ctx.profile_read()
+    ctx.profile(False)
+    clocks = sampler.stop()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    got = [o.cpu().numpy() for o in outs]
+    ok = all(np.array_equal(a, ref_out[k]) for a, k in zip(got, ("abs", "marg", "yaw")))
+    value = ws * rays_per_step * args.steps / (total_ms / 1e3)
+    # ---- end to end: host arrays through the public call (copies in the timed region)
+    e2e_ms = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(np.sum(e2e_ms))
+    if ws > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = ws * rays_per_step * len(e2e_ms) / (e2e_total / 1e3)
+    # ---- roofline of the dominant kernel (count pass): algorithmic gather bytes per launch
+    count_launches = max(1, int(ktimes["count_launches"]))
+    alg_bytes_step = stats["dda_steps"] * 1 + stats["depth_reads"] * 4
+    launches_per_step = count_launches / args.steps
+    alg_bytes_launch = alg_bytes_step / launches_per_step
+    avg_launch_s = ktimes["count_ms"] / 1e3 / count_launches
+    achieved = alg_bytes_launch / avg_launch_s / 1e9
+    peak, peak_kind = load_peaks()
+    traffic = profiled_traffic("count_kernel", args.workload)
+    n_launches = int(ktimes["count_launches"] + ktimes["select_launches"] + ktimes["render_launches"] +
+                     ktimes["plan_launches"] * 4)
+    res = None
+    if rank == 0:
+        res = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "rays/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int32/int64 fixed point (u8 map)",
+            "data": "synthetic (seeded; stands in for the paper's Gazebo worlds)",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "nodes": n, "yaw_bins": s.yaw_bins,
+                       "rays_per_node_yaw": s.width * s.height, "max_depth": max_depth,
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
+            "replans_per_s": ws * args.steps / (total_ms / 1e3),
+            "nodes_per_s": ws * n * args.steps / (total_ms / 1e3),
+            "replan_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "results_match_host_path": bool(ok),
+            "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": int(n * 16),
+                    "d2h_bytes_per_step": int(n * 12), "ms_per_step": e2e_total / len(e2e_ms)},
+            "gpu_launches": n_launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel": "count_kernel",
+                         "algorithmic_bytes_per_launch": alg_bytes_launch,
+                         "avg_launch_ms": avg_launch_s * 1e3,
+                         "note": "algorithmic bytes = DDA voxel gathers (1 B) + ancestor depth reads (4 B)"},
+            "work_per_step": stats,
+            "kernel_ms_per_step": {k.replace("_ms", ""): v / args.steps for k, v in ktimes.items() if k.endswith("_ms")},
+            "clocks": clocks,
+        }
+    m.close()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return res
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(workload, sample_depth=None, budget_s=20.0):
+    """The oracle as it stands, on this host's cores, on a bounded, ancestor-closed sample of
+    the workload (all nodes up to a depth), reported in the benchmark's unit."""
+    import oracle
+    prob = make_problem(workload, 0)
+    s = prob.sensor
+    d = prob.tree.depth()
+    if sample_depth is None:
+        sample_depth = {"tiny": 10, "paper_scale": 5, "large": 1}.get(workload, 3)
+    mask = (d <= sample_depth).astype(np.uint8)
+    m = int(mask.sum())
+    t0 = time.perf_counter()
+    oracle.eval_tree(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent, prob.tree.pos, s,
+                     node_mask=mask)
+    dt = time.perf_counter() - t0
+    rays = m * s.yaw_bins * s.width * s.height
+    return {"value": rays / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
+                      f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    cb = None
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args.workload)
+        if i >= args.warmup:
+            vals.append(r["value"])
+        cb = r
+    value = float(np.mean(vals))
+    cb = dict(cb)
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": cb["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64 fixed point (u8 map)", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "sample": cb["sample"]},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_scale",
+                    choices=["paper_scale", "tiny", "large", "batched", "serving"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if args.workload == "batched":
+        from paper_2609_40297_gb300 import workloads
+        res = workloads.bench_batched(args)
+    elif args.workload == "serving":
+        from paper_2609_40297_gb300 import workloads
+        res = workloads.bench_serving(args)
+    else:
+        res = run_ours(args)
+    ws, rank, _ = dist_env()
+    if rank == 0 and res is not None:
+        if ws == 1 and not args.no_cpu_baseline and args.workload in ("paper_scale", "tiny", "large"):
+            cb = cpu_baseline(args.workload)
+            res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

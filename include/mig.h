@@ -1,0 +1,212 @@
+/*
+ * mig.h — path-dependent marginal information gain over an RRT planning tree, on one GPU.
+ *
+ * The method: each tree node n is a candidate viewpoint (position p_n, yaw psi_n) in a voxel
+ * map of free / occupied / unknown voxels (Sec. III-A). Its absolute gain counts the unknown
+ * voxels visible from it (Eq. 1); its marginal gain counts those that no ancestor on its
+ * path already observes (Eq. 2). Previous observations are depth buffers: each node keeps
+ * the depth buffer of its selected yaw (Sec. IV-A), and every unknown-voxel sample of a
+ * candidate ray is projected into its ancestors' buffers (Eq. 5) and dropped when its depth
+ * is smaller than or equal to the stored one (Sec. IV-B). Nodes are evaluated level by level
+ * in depth order, nodes and rays of a level in parallel (Sec. IV-C).
+ *
+ * Conventions (all calls):
+ *  - Status codes are returned, never abort. mig_last_error() gives a thread-local message.
+ *  - Host pointers are caller-owned and only read/written during the call unless stated.
+ *  - Maps, contexts and servers are library-owned objects, destroyed by their _destroy call.
+ *  - Gains are integer voxel counts; the volume of Eq. 1 is count * voxel_size^3.
+ *  - Depth buffers hold the camera z in Q16.16 voxel units (uint32).
+ *  - Grids are x-fastest: index = (z * ny + y) * nx + x, codes 0 unknown, 1 free, 2 occupied.
+ *  - World frame z-up; yaw bin k is psi_k = 2 pi k / K counter-clockwise from +x; camera
+ *    x right, y down, z forward; pitch positive = nose down; pinhole with principal point at
+ *    the image centre and rays through pixel centres (Eq. 5).
+ *  - The exact integer arithmetic is specified in the project's design notes; results are
+ *    deterministic and identical on every run.
+ */
+#ifndef MIG_H
+#define MIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MIG_ABI_VERSION 1
+#define MIG_MAX_DEPTH 64        /* deepest node (root = 0) */
+#define MIG_MAX_DIM 4096        /* voxels per grid axis */
+#define MIG_MAX_IMAGE 2048      /* rays (pixels) per image axis */
+#define MIG_MAX_YAW_BINS 1024
+#define MIG_MAX_RANGE_VOXELS 1024
+
+typedef enum {
+    MIG_OK = 0,
+    MIG_EINVAL = 1,   /* invalid argument: bad code, tree, sensor, size or position */
+    MIG_ENOMEM = 2,   /* device or host allocation failed; nothing leaked */
+    MIG_ECUDA = 3,    /* a CUDA call failed (message in mig_last_error) */
+    MIG_ETIMEOUT = 4, /* a bounded wait (device queue or poll) ran out */
+    MIG_EBUSY = 5,    /* not finished yet (server poll) or object in use */
+    MIG_ENOTFOUND = 6 /* unknown ticket */
+} mig_status;
+
+typedef struct mig_ctx mig_ctx;
+typedef struct mig_map mig_map;
+
+/* Device memory provider. alloc returns device memory of `bytes` usable on `stream`
+ * (NULL on failure); free releases it (stream-ordered). NULL allocator = cudaMallocAsync. */
+typedef struct mig_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} mig_allocator;
+
+/* Depth camera (Sec. IV-A, Sec. V): field of view, ray grid = depth-buffer size W x H,
+ * maximum range d_max, number of candidate yaws K, and camera pitch. Limits: 0 < fov < 180,
+ * 1 <= W, H <= MIG_MAX_IMAGE, 1 <= K <= MIG_MAX_YAW_BINS, -90 <= pitch <= 90,
+ * 0 < range / voxel_size <= MIG_MAX_RANGE_VOXELS, focal lengths W/2/tan(hfov/2) < 2^15 - W. */
+typedef struct mig_sensor {
+    float hfov_deg, vfov_deg;
+    int32_t width, height;
+    float range_m;
+    int32_t yaw_bins;
+    float pitch_deg;
+} mig_sensor;
+
+/* Gain formulation (Sec. III-B, Sec. V-A): marginal over all ancestors (Eq. 2, the default),
+ * single-parent exclusion g_sp, or absolute gain (Eq. 1, no exclusion; yaw = argmax abs). */
+typedef enum { MIG_MODE_MARGINAL = 0, MIG_MODE_SINGLE_PARENT = 1, MIG_MODE_ABSOLUTE = 2 } mig_mode;
+
+/* ---------------------------------------------------------------------------------------
+ * Context: one GPU, one CUDA stream, one allocator. `stream` is a cudaStream_t (NULL = the
+ * legacy default stream). Thread-compatible: one thread at a time per context.
+ * Errors: MIG_EINVAL (bad device), MIG_ECUDA, MIG_ENOMEM.
+ * --------------------------------------------------------------------------------------- */
+mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocator, mig_ctx **out);
+void mig_ctx_destroy(mig_ctx *ctx);
+mig_status mig_ctx_set_stream(mig_ctx *ctx, void *stream);
+/* Waits for all work on the context's stream; returns MIG_EINVAL if a device-side check of an
+ * earlier asynchronous call (mig_tree_eval_device) failed since the last sync. */
+mig_status mig_ctx_sync(mig_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Voxel map (Sec. III-A): nx*ny*nz voxels of edge voxel_size_m, voxel (0,0,0)'s low corner
+ * at origin_m. host_voxels: x-fastest codes, copied to the device (NULL = all unknown).
+ * The device copy is library-owned, kept resident until mig_map_destroy.
+ * Errors: MIG_EINVAL (dims outside [1, MIG_MAX_DIM], voxel_size <= 0, a code > 2).
+ * --------------------------------------------------------------------------------------- */
+mig_status mig_map_create(mig_ctx *ctx, int nx, int ny, int nz, float voxel_size_m, const float origin_m[3],
+                          const uint8_t *host_voxels, mig_map **out);
+/* Overwrites the box [x0,x0+dx) x [y0,y0+dy) x [z0,z0+dz) from host_voxels (x-fastest, dx*dy*dz).
+ * Ordered on the context stream after earlier evaluations (they see the old contents).
+ * Errors: MIG_EINVAL (box outside the grid, empty box, a code > 2). */
+mig_status mig_map_update(mig_map *map, int x0, int y0, int z0, int dx, int dy, int dz,
+                          const uint8_t *host_voxels);
+/* Reads the whole grid back (x-fastest, nx*ny*nz bytes). */
+mig_status mig_map_read(mig_map *map, uint8_t *host_out);
+void mig_map_destroy(mig_map *map);
+
+/* Depth-buffer resolution rule of Sec. IV-A: W = ceil(2 d_max tan(hfov/2) / v),
+ * H = ceil(2 d_max tan(vfov/2) / v), so that one pixel at range is one voxel. Host only. */
+mig_status mig_default_resolution(const mig_sensor *sensor, float voxel_size_m, int32_t *width, int32_t *height);
+
+/* Tree check and depth (Sec. III-B, Sec. IV-C): exactly one root (parent -1), parents in
+ * [0, n), no cycles, depth <= MIG_MAX_DEPTH. depth_out (nullable, n) receives each node's
+ * depth, max_depth_out (nullable) the largest. Host only, no GPU needed. MIG_EINVAL if invalid. */
+mig_status mig_tree_check(int n, const int32_t *parent, int32_t *depth_out, int32_t *max_depth_out);
+
+/* ---------------------------------------------------------------------------------------
+ * Tree evaluation, host arrays (Sec. IV-C). parent[n] (-1 = root), pos_m[n*3] world metres.
+ * Outputs (host, n each): abs_gain = max over yaws of the absolute count (Eq. 1),
+ * marg_gain = marginal count at the selected yaw (Eq. 2), best_yaw = lowest k maximising the
+ * marginal count. Synchronous: returns when the outputs are written. Each position must lie
+ * inside the grid box. n = 0 is a no-op.
+ * Errors: MIG_EINVAL (tree, sensor, positions), MIG_ENOMEM, MIG_ECUDA.
+ * --------------------------------------------------------------------------------------- */
+mig_status mig_tree_eval(mig_map *map, int n, const int32_t *parent, const float *pos_m, const mig_sensor *sensor,
+                         int32_t *abs_gain, int32_t *marg_gain, int32_t *best_yaw);
+
+/* Extended evaluation: a gain mode and optional diagnostic outputs (host, nullable):
+ * per-(node, yaw) counts [n][K] and every node's selected depth buffer [n][H][W]. */
+typedef struct mig_eval_opts {
+    int32_t mode;           /* mig_mode */
+    int32_t *counts_abs;    /* n*K or NULL */
+    int32_t *counts_marg;   /* n*K or NULL (the mode's exclusion count) */
+    uint32_t *depth_buffers;/* n*H*W or NULL: D_n at best_yaw, Q16.16 voxel units */
+} mig_eval_opts;
+mig_status mig_tree_eval_ex(mig_map *map, int n, const int32_t *parent, const float *pos_m, const mig_sensor *sensor,
+                            const mig_eval_opts *opts, int32_t *abs_gain, int32_t *marg_gain, int32_t *best_yaw);
+
+/* Device-resident evaluation: parent, pos_m and the three outputs are DEVICE pointers; the
+ * tree is planned on the device; the call only enqueues work on the context stream and
+ * returns. max_depth bounds the tree's depth (levels launched = max_depth + 1; a deeper node,
+ * a cycle, a second root or an out-of-grid position is flagged on the device, all outputs
+ * are then -1 and the next mig_ctx_sync returns MIG_EINVAL).
+ * Errors at call time: MIG_EINVAL (sensor, n, max_depth), MIG_ENOMEM, MIG_ECUDA. */
+mig_status mig_tree_eval_device(mig_map *map, int n, const int32_t *parent, const float *pos_m,
+                                const mig_sensor *sensor, int max_depth, int32_t *abs_gain, int32_t *marg_gain,
+                                int32_t *best_yaw);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched evaluation: many independent trees (each on its own map and sensor) in one
+ * persistent launch with per-level device work queues, replayed from a captured CUDA graph
+ * when the batch's shape repeats. Host arrays as in mig_tree_eval; results are identical to
+ * n_trees separate mig_tree_eval calls. Synchronous.
+ * Errors: as mig_tree_eval (the first failing tree's status), MIG_ETIMEOUT (a device-side
+ * dependency wait ran out; no output is then valid).
+ * --------------------------------------------------------------------------------------- */
+typedef struct mig_tree_desc {
+    mig_map *map;
+    int32_t n_nodes;
+    const int32_t *parent; /* host, n_nodes */
+    const float *pos_m;    /* host, n_nodes*3 */
+    mig_sensor sensor;
+    int32_t mode;          /* mig_mode */
+    int32_t *abs_gain;     /* host outputs, n_nodes each */
+    int32_t *marg_gain;
+    int32_t *best_yaw;
+} mig_tree_desc;
+mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_tree_desc *trees);
+
+/* Tile shape of the batched kernel (chosen by the autotuner; exposed for the tuner and tests). */
+typedef struct mig_tile_config {
+    int32_t tile_w, tile_h;   /* pixels per work item (tile_w * tile_h threads per CTA) */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM */
+} mig_tile_config;
+mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg);
+mig_status mig_batch_get_tiles(mig_ctx *ctx, mig_tile_config *cfg);
+
+
+/* ---------------------------------------------------------------------------------------
+ * Measurement (no counterpart in the paper; used by the benchmark's roofline figures).
+ * mig_ctx_profile(ctx, 1) starts recording a CUDA event pair around every kernel the
+ * library launches on the context stream (0 stops); mig_ctx_profile_read synchronises and
+ * returns the summed device time and launch count per kernel kind since the last read.
+ * mig_tree_eval_stats runs mig_tree_eval with an instrumented count pass and returns the
+ * algorithmic work: rays cast, DDA steps (1-byte voxel gathers), owner tests, samples,
+ * ancestor projections and depth texels read (4 B each). Results are identical to
+ * mig_tree_eval; the instrumented pass is slower and is not meant to be timed.
+ * --------------------------------------------------------------------------------------- */
+typedef struct mig_kernel_times {
+    double count_ms, select_ms, render_ms, plan_ms, batch_ms;
+    uint64_t count_launches, select_launches, render_launches, plan_launches, batch_launches;
+} mig_kernel_times;
+mig_status mig_ctx_profile(mig_ctx *ctx, int enable);
+mig_status mig_ctx_profile_read(mig_ctx *ctx, mig_kernel_times *out);
+
+typedef struct mig_eval_stats {
+    uint64_t rays, dda_steps, unknown_visits, samples, ancestor_tests, depth_reads;
+    uint64_t render_rays, render_steps;
+    uint64_t count_launches, render_launches;
+} mig_eval_stats;
+mig_status mig_tree_eval_stats(mig_map *map, int n, const int32_t *parent, const float *pos_m,
+                               const mig_sensor *sensor, mig_eval_stats *stats, int32_t *abs_gain,
+                               int32_t *marg_gain, int32_t *best_yaw);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *mig_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIG_H */

@@ -1,0 +1,334 @@
+"""Python binding of libmig.so: path-dependent marginal information gain on one GB300.
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels. PyTorch
+provides device memory (the caching allocator plugs into the library's allocator hook) and
+streams. There is no CPU fallback: if libmig.so is missing or cannot load, importing the
+binding's entry points raises.
+
+Names follow the C ABI in include/mig.h (mig_ctx_create -> Context, mig_map_create -> Map,
+mig_tree_eval -> tree_eval, ...).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmig.so")
+
+MIG_OK, MIG_EINVAL, MIG_ENOMEM, MIG_ECUDA, MIG_ETIMEOUT, MIG_EBUSY, MIG_ENOTFOUND = range(7)
+MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE = 0, 1, 2
+STATUS_NAMES = {0: "MIG_OK", 1: "MIG_EINVAL", 2: "MIG_ENOMEM", 3: "MIG_ECUDA", 4: "MIG_ETIMEOUT", 5: "MIG_EBUSY",
+                6: "MIG_ENOTFOUND"}
+
+# every symbol declared in include/mig.h
+EXPORTS = [
+    "mig_ctx_create", "mig_ctx_destroy", "mig_ctx_set_stream", "mig_ctx_sync",
+    "mig_map_create", "mig_map_update", "mig_map_read", "mig_map_destroy",
+    "mig_default_resolution", "mig_tree_check",
+    "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device",
+    "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles",
+    "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
+]
+
+
+class MigError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Sensor(C.Structure):
+    _fields_ = [("hfov_deg", C.c_float), ("vfov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("range_m", C.c_float), ("yaw_bins", C.c_int32), ("pitch_deg", C.c_float)]
+
+    @classmethod
+    def of(cls, s):
+        if isinstance(s, cls):
+            return s
+        return cls(float(s.hfov_deg), float(s.vfov_deg), int(s.width), int(s.height), float(s.range_m),
+                   int(s.yaw_bins), float(s.pitch_deg))
+
+
+class EvalOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("counts_abs", C.c_void_p), ("counts_marg", C.c_void_p),
+                ("depth_buffers", C.c_void_p)]
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("map", C.c_void_p), ("n_nodes", C.c_int32), ("parent", C.c_void_p), ("pos_m", C.c_void_p),
+                ("sensor", Sensor), ("mode", C.c_int32), ("abs_gain", C.c_void_p), ("marg_gain", C.c_void_p),
+                ("best_yaw", C.c_void_p)]
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("count_ms", C.c_double), ("select_ms", C.c_double), ("render_ms", C.c_double),
+                ("plan_ms", C.c_double), ("batch_ms", C.c_double), ("count_launches", C.c_uint64),
+                ("select_launches", C.c_uint64), ("render_launches", C.c_uint64), ("plan_launches", C.c_uint64),
+                ("batch_launches", C.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class EvalStats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("rays", "dda_steps", "unknown_visits", "samples", "ancestor_tests",
+                                          "depth_reads", "render_rays", "render_steps", "count_launches",
+                                          "render_launches")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class TileConfig(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libmig.so (built in-tree by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            p, i, f = C.c_void_p, C.c_int, C.c_float
+            st = C.c_int
+            sig = {
+                "mig_ctx_create": (st, [i, p, p, p]),
+                "mig_ctx_destroy": (None, [p]),
+                "mig_ctx_set_stream": (st, [p, p]),
+                "mig_ctx_sync": (st, [p]),
+                "mig_map_create": (st, [p, i, i, i, f, p, p, p]),
+                "mig_map_update": (st, [p, i, i, i, i, i, i, p]),
+                "mig_map_read": (st, [p, p]),
+                "mig_map_destroy": (None, [p]),
+                "mig_default_resolution": (st, [p, f, p, p]),
+                "mig_tree_check": (st, [i, p, p, p]),
+                "mig_tree_eval": (st, [p, i, p, p, p, p, p, p]),
+                "mig_tree_eval_ex": (st, [p, i, p, p, p, p, p, p, p]),
+                "mig_tree_eval_device": (st, [p, i, p, p, p, i, p, p, p]),
+                "mig_tree_eval_batch": (st, [p, i, p]),
+                "mig_batch_set_tiles": (st, [p, p]),
+                "mig_batch_get_tiles": (st, [p, p]),
+                "mig_server_create": (st, [p, C.c_size_t, i, p]),
+                "mig_server_submit": (st, [p, p, p]),
+                "mig_server_poll": (st, [p, C.c_uint64, C.c_int64]),
+                "mig_server_map_update": (st, [p, p, i, i, i, i, i, i, p]),
+                "mig_server_timing": (st, [p, C.c_uint64, p, p, p]),
+                "mig_server_destroy": (None, [p]),
+                "mig_ctx_profile": (st, [p, i]),
+                "mig_ctx_profile_read": (st, [p, p]),
+                "mig_tree_eval_stats": (st, [p, i, p, p, p, p, p, p, p]),
+                "mig_last_error": (C.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().mig_last_error().decode()
+
+
+def check(status):
+    if status != MIG_OK:
+        raise MigError(status, last_error())
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _torch_allocator(device):
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:  # out of memory -> NULL -> MIG_ENOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return Allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+
+
+class Context:
+    """mig_ctx: one GPU, one stream (default: torch's current stream), torch's allocator."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._alloc = _torch_allocator(device) if torch_allocator else None
+        out = C.c_void_p()
+        check(lib().mig_ctx_create(device, C.c_void_p(handle),
+                                   C.byref(self._alloc) if self._alloc is not None else None, C.byref(out)))
+        self.h = out
+
+    def sync(self):
+        check(lib().mig_ctx_sync(self.h))
+
+    def set_tiles(self, tile_w, tile_h, ctas_per_sm=4):
+        check(lib().mig_batch_set_tiles(self.h, C.byref(TileConfig(tile_w, tile_h, ctas_per_sm))))
+
+    def get_tiles(self):
+        t = TileConfig()
+        check(lib().mig_batch_get_tiles(self.h, C.byref(t)))
+        return (t.tile_w, t.tile_h, t.ctas_per_sm)
+
+    def profile(self, enable=True):
+        check(lib().mig_ctx_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        t = KernelTimes()
+        check(lib().mig_ctx_profile_read(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mig_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Map:
+    """mig_map: a device-resident voxel grid (codes 0 unknown, 1 free, 2 occupied)."""
+
+    def __init__(self, ctx: Context, grid, voxel_size, origin=(0.0, 0.0, 0.0)):
+        g = None if grid is None else _host(grid, np.uint8)
+        if g is None:
+            raise ValueError("grid is required (shape nz, ny, nx)")
+        nz, ny, nx = g.shape
+        org = (C.c_float * 3)(*[float(x) for x in origin])
+        out = C.c_void_p()
+        check(lib().mig_map_create(ctx.h, nx, ny, nz, float(voxel_size), org, _ptr(g), C.byref(out)))
+        self.h = out
+        self.ctx = ctx
+        self.shape = (nz, ny, nx)
+        self.voxel_size = float(voxel_size)
+        self.origin = tuple(float(x) for x in origin)
+
+    def update(self, x0, y0, z0, box):
+        b = _host(box, np.uint8)
+        dz, dy, dx = b.shape
+        check(lib().mig_map_update(self.h, x0, y0, z0, dx, dy, dz, _ptr(b)))
+
+    def read(self):
+        out = np.empty(self.shape, np.uint8)
+        check(lib().mig_map_read(self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mig_map_destroy(self.h)
+            self.h = None
+
+
+def default_resolution(sensor, voxel_size):
+    w, h = C.c_int32(), C.c_int32()
+    s = Sensor.of(sensor)
+    check(lib().mig_default_resolution(C.byref(s), float(voxel_size), C.byref(w), C.byref(h)))
+    return w.value, h.value
+
+
+def tree_check(parent):
+    parent = _host(parent, np.int32)
+    depth = np.zeros(parent.shape[0], np.int32)
+    md = C.c_int32()
+    check(lib().mig_tree_check(parent.shape[0], _ptr(parent), _ptr(depth), C.byref(md)))
+    return depth, md.value
+
+
+def tree_eval(m: Map, parent, pos, sensor, mode=MODE_MARGINAL, want_counts=False, want_depth=False):
+    """mig_tree_eval(_ex) on host arrays; returns dict(abs, marg, yaw[, cnt_abs, cnt_marg, depth])."""
+    parent = _host(parent, np.int32)
+    pos = _host(pos, np.float32).reshape(-1, 3)
+    n = parent.shape[0]
+    s = Sensor.of(sensor)
+    out = {k: np.zeros(n, np.int32) for k in ("abs", "marg", "yaw")}
+    opts = EvalOpts(int(mode), None, None, None)
+    if want_counts:
+        out["cnt_abs"] = np.zeros((n, s.yaw_bins), np.int32)
+        out["cnt_marg"] = np.zeros((n, s.yaw_bins), np.int32)
+        opts.counts_abs = out["cnt_abs"].ctypes.data
+        opts.counts_marg = out["cnt_marg"].ctypes.data
+    if want_depth:
+        out["depth"] = np.zeros((n, s.height, s.width), np.uint32)
+        opts.depth_buffers = out["depth"].ctypes.data
+    check(lib().mig_tree_eval_ex(m.h, n, _ptr(parent), _ptr(pos), C.byref(s), C.byref(opts), _ptr(out["abs"]),
+                                 _ptr(out["marg"]), _ptr(out["yaw"])))
+    return out
+
+
+def tree_eval_stats(m: Map, parent, pos, sensor):
+    """mig_tree_eval_stats: results plus the algorithmic work of the count and render passes."""
+    parent = _host(parent, np.int32)
+    pos = _host(pos, np.float32).reshape(-1, 3)
+    n = parent.shape[0]
+    s = Sensor.of(sensor)
+    out = {k: np.zeros(n, np.int32) for k in ("abs", "marg", "yaw")}
+    st = EvalStats()
+    check(lib().mig_tree_eval_stats(m.h, n, _ptr(parent), _ptr(pos), C.byref(s), C.byref(st), _ptr(out["abs"]),
+                                    _ptr(out["marg"]), _ptr(out["yaw"])))
+    return out, st.as_dict()
+
+
+def tree_eval_device(m: Map, parent_dev, pos_dev, sensor, max_depth, abs_dev, marg_dev, yaw_dev):
+    """mig_tree_eval_device: torch CUDA tensors in and out; enqueued on the context stream."""
+    n = int(parent_dev.shape[0])
+    s = Sensor.of(sensor)
+    check(lib().mig_tree_eval_device(m.h, n, C.c_void_p(parent_dev.data_ptr()), C.c_void_p(pos_dev.data_ptr()),
+                                     C.byref(s), int(max_depth), C.c_void_p(abs_dev.data_ptr()),
+                                     C.c_void_p(marg_dev.data_ptr()), C.c_void_p(yaw_dev.data_ptr())))
+
+
+def tree_eval_batch(ctx: Context, problems, maps, mode=MODE_MARGINAL):
+    """mig_tree_eval_batch over (parent, pos, sensor) problems on the given maps."""
+    descs = (TreeDesc * len(problems))()
+    keep, outs = [], []
+    for i, ((parent, pos, sensor), m) in enumerate(zip(problems, maps)):
+        parent = _host(parent, np.int32)
+        pos = _host(pos, np.float32).reshape(-1, 3)
+        n = parent.shape[0]
+        o = {k: np.zeros(n, np.int32) for k in ("abs", "marg", "yaw")}
+        keep += [parent, pos]
+        outs.append(o)
+        descs[i] = TreeDesc(m.h.value, n, parent.ctypes.data, pos.ctypes.data, Sensor.of(sensor), int(mode),
+                            o["abs"].ctypes.data, o["marg"].ctypes.data, o["yaw"].ctypes.data)
+    check(lib().mig_tree_eval_batch(ctx.h, len(problems), descs))
+    return outs

@@ -1,0 +1,481 @@
+// Device kernels: fused per-level count (3D DDA + owner test + ancestor depth test + integer
+// reductions), yaw selection, depth-buffer render, map brick scatter/gather, device planning.
+//
+// All result-deciding arithmetic is integer (the fixed-point reading of Sec. IV-A..C):
+// positions Q16 voxel units, ray directions Q30, projection rows Q16, depths Q16.16.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+#include "mig.h"
+
+namespace mig {
+
+namespace {
+
+constexpr int kOcc = 2;
+constexpr int kUnknown = 0;
+constexpr uint32_t kQ16 = 65536;
+
+__device__ __forceinline__ uint32_t brick_addr(const GridView &G, int x, int y, int z) {
+    const uint32_t b = ((uint32_t)(z >> 3) * (uint32_t)G.nby + (uint32_t)(y >> 3)) * (uint32_t)G.nbx + (uint32_t)(x >> 3);
+    return (b << 9) | ((uint32_t)(z & 7) << 6) | ((uint32_t)(y & 7) << 3) | (uint32_t)(x & 7);
+}
+
+// Per-axis DDA set-up (Sec. IV-B, Amanatides-Woo). n = distance to the next face (Q16),
+// ad = |d| (Q30); rem = number of face crossings along this axis that stay inside the grid
+// and start before the range T (crossing k is at t = (n + k 2^16) / ad, allowed iff < T).
+__device__ __forceinline__ void axis_init(int P, int d, int N, int64_t Tq, int &v, uint32_t &n, uint32_t &ad, int &s,
+                                          int &rem) {
+    v = P >> 16;
+    int grid_rem;
+    if (d > 0) {
+        s = 1;
+        ad = (uint32_t)d;
+        n = (uint32_t)(((v + 1) << 16) - P);
+        grid_rem = N - 1 - v;
+    } else if (d < 0) {
+        s = -1;
+        ad = (uint32_t)(-d);
+        n = (uint32_t)(P - (v << 16));
+        grid_rem = v;
+    } else {
+        s = 0;
+        ad = 0;
+        n = kQ16;
+        rem = 0;
+        return;
+    }
+    const uint64_t lim = ((uint64_t)Tq * ad + ((1ull << 30) - 1)) >> 30;  // n >= lim  <=>  t >= T
+    const int64_t range_rem = (n >= lim) ? 0 : (int64_t)((lim - n + (kQ16 - 1)) >> 16);
+    rem = (int)min((int64_t)grid_rem, range_rem);
+}
+
+// floor(U / Z) for 0 <= U < bound * Z, Z > 0: float estimate, exact integer correction.
+__device__ __forceinline__ int floor_div_bounded(int64_t U, int64_t Z, int bound) {
+    int q = (int)__fdividef(__ll2float_rn(U), __ll2float_rn(Z));
+    q = max(0, min(q, bound - 1));
+    while (q > 0 && (int64_t)q * Z > U) --q;
+    while (q < bound - 1 && (int64_t)(q + 1) * Z <= U) ++q;
+    return q;
+}
+
+struct AncRec {
+    int px, py, pz;
+    int m[9];
+    const uint32_t *D;
+};
+
+struct RayIn {
+    int vx, vy, vz;
+    uint32_t nx, ny, nz, adx, ady, adz;
+    int sx, sy, sz, rx, ry, rz;
+};
+
+__device__ __forceinline__ void ray_init(RayIn &r, const GridView &G, int Px, int Py, int Pz, int dx, int dy, int dz,
+                                         int64_t Tq) {
+    axis_init(Px, dx, G.nx, Tq, r.vx, r.nx, r.adx, r.sx, r.rx);
+    axis_init(Py, dy, G.ny, Tq, r.vy, r.ny, r.ady, r.sy, r.ry);
+    axis_init(Pz, dz, G.nz, Tq, r.vz, r.nz, r.adz, r.sz, r.rz);
+}
+
+// World direction of (yaw k, pixel): yaw rotation of the body-frame ray, floored (Q30).
+__device__ __forceinline__ void ray_dir(const int4 b, int ck, int sk, int &dx, int &dy, int &dz) {
+    const int64_t bx = b.x, by = b.y;
+    dx = (int)(((int64_t)ck * bx - (int64_t)sk * by) >> 30);
+    dy = (int)(((int64_t)sk * bx + (int64_t)ck * by) >> 30);
+    dz = b.z;
+}
+
+// One step of the DDA: picks the axis with the smallest next crossing (ties x, y, z), stops if
+// that crossing leaves the grid or starts at t >= T. Returns false when the ray ends.
+__device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) {
+    const uint64_t xy = (uint64_t)r.nx * r.ady, yx = (uint64_t)r.ny * r.adx;
+    const uint64_t xz = (uint64_t)r.nx * r.adz, zx = (uint64_t)r.nz * r.adx;
+    const uint64_t yz = (uint64_t)r.ny * r.adz, zy = (uint64_t)r.nz * r.ady;
+    if (xy <= yx && xz <= zx) {
+        if (r.rx == 0) return false;
+        --r.rx;
+        ne = r.nx;
+        ade = r.adx;
+        r.nx += kQ16;
+        r.vx += r.sx;
+    } else if (yz <= zy) {
+        if (r.ry == 0) return false;
+        --r.ry;
+        ne = r.ny;
+        ade = r.ady;
+        r.ny += kQ16;
+        r.vy += r.sy;
+    } else {
+        if (r.rz == 0) return false;
+        --r.rz;
+        ne = r.nz;
+        ade = r.adz;
+        r.nz += kQ16;
+        r.vz += r.sz;
+    }
+    return true;
+}
+
+// Depth (Q16.16 voxel units, camera z) of the entry point t_e = ne / ade of the hit voxel, or
+// of the range endpoint.
+__device__ __forceinline__ uint32_t hit_depth(bool hit, uint32_t ne, uint32_t ade, int dzc, int64_t Tq) {
+    if (hit) return (uint32_t)(((uint64_t)ne * (uint32_t)dzc) / ade);
+    return (uint32_t)(((uint64_t)Tq * (uint32_t)dzc) >> 30);
+}
+
+__device__ __forceinline__ void decode_item(const LevelParams &p, int item, int &li, int &k, int &tile) {
+    tile = item % p.tiles;
+    const int rest = item / p.tiles;
+    k = rest % p.K;
+    li = rest / p.K;
+}
+
+// ------------------------------------------------------------------------------- count kernel
+// One CTA handles one work item (node of the level, yaw, tile of tile_w x tile_h pixel rays),
+// grid-striding over the level's items. Each thread casts one ray; unknown voxels owned by the
+// ray (A1: the voxel centre projects into this pixel) count as absolute gain, and as marginal
+// gain unless an ancestor's depth buffer observes the centre (Sec. IV-B).
+template <bool STATS>
+__global__ void __launch_bounds__(256) count_kernel(const LevelParams p) {
+    __shared__ AncRec s_anc[MIG_MAX_DEPTH];
+    __shared__ int s_abs, s_mrg;
+    const int l0 = p.level_off[p.lvl];
+    const int L = p.level_off[p.lvl + 1] - l0;
+    const int items = L * p.K * p.tiles;
+    const int tid = threadIdx.x;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        int li, k, tile;
+        decode_item(p, item, li, k, tile);
+        const int n = p.level_nodes[l0 + li];
+        const int4 nd = p.node[n];
+        const int2 ar = p.anc_range[n];
+        int na = ar.y;
+        if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
+        else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
+        for (int t = tid; t < na; t += blockDim.x) {
+            const int a = p.anc[ar.x + t];
+            const int4 an = p.node[a];
+            const int32_t *y = p.yawtab + p.sel_yaw[a] * 12;
+            AncRec r;
+            r.px = an.x;
+            r.py = an.y;
+            r.pz = an.z;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) r.m[q] = y[2 + q];
+            r.D = p.arena + (size_t)an.w * p.W * p.H;
+            s_anc[t] = r;
+        }
+        if (tid == 0) {
+            s_abs = 0;
+            s_mrg = 0;
+        }
+        __syncthreads();
+        const int32_t *yk = p.yawtab + k * 12;
+        const int ck = yk[0], sk = yk[1];
+        const int mu0 = yk[2], mu1 = yk[3], mu2 = yk[4];
+        const int mv0 = yk[5], mv1 = yk[6], mv2 = yk[7];
+        const int mz0 = yk[8], mz1 = yk[9], mz2 = yk[10];
+        const int ti = (tile % p.tiles_x) * p.tile_w + tid % p.tile_w;
+        const int tj = (tile / p.tiles_x) * p.tile_h + tid / p.tile_w;
+        int c_abs = 0, c_mrg = 0;
+        uint32_t st_steps = 0, st_unk = 0, st_anc = 0, st_reads = 0;
+        if (ti < p.W && tj < p.H) {
+            const int4 b = p.body[tj * p.W + ti];
+            int dx, dy, dz;
+            ray_dir(b, ck, sk, dx, dy, dz);
+            RayIn r;
+            ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
+            uint32_t ne = 0, ade = 1;
+            for (;;) {
+                const uint8_t code = __ldg(p.grid.g + brick_addr(p.grid, r.vx, r.vy, r.vz));
+                if constexpr (STATS) ++st_steps;
+                if (code == kOcc) break;
+                if (code == kUnknown) {
+                    if constexpr (STATS) ++st_unk;
+                    // owner test: centre of this voxel projects into pixel (ti, tj)
+                    const int rx = (r.vx << 16) + 32768 - nd.x;
+                    const int ry = (r.vy << 16) + 32768 - nd.y;
+                    const int rz = (r.vz << 16) + 32768 - nd.z;
+                    const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * rz;
+                    if (Z > 0) {
+                        const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * rz;
+                        const int64_t iZ = (int64_t)ti * Z;
+                        if (U >= iZ && U < iZ + Z) {
+                            const int64_t V = (int64_t)mv0 * rx + (int64_t)mv1 * ry + (int64_t)mv2 * rz;
+                            const int64_t jZ = (int64_t)tj * Z;
+                            if (V >= jZ && V < jZ + Z) {
+                                ++c_abs;
+                                bool seen = false;
+                                for (int a = 0; a < na && !seen; ++a) {
+                                    const AncRec &A = s_anc[a];
+                                    const int ax = (r.vx << 16) + 32768 - A.px;
+                                    const int ay = (r.vy << 16) + 32768 - A.py;
+                                    const int az = (r.vz << 16) + 32768 - A.pz;
+                                    const int64_t Za = (int64_t)A.m[6] * ax + (int64_t)A.m[7] * ay + (int64_t)A.m[8] * az;
+                                    if constexpr (STATS) ++st_anc;
+                                    if (Za <= 0) continue;
+                                    const int64_t Ua = (int64_t)A.m[0] * ax + (int64_t)A.m[1] * ay + (int64_t)A.m[2] * az;
+                                    if (Ua < 0 || Ua >= (int64_t)p.W * Za) continue;
+                                    const int64_t Va = (int64_t)A.m[3] * ax + (int64_t)A.m[4] * ay + (int64_t)A.m[5] * az;
+                                    if (Va < 0 || Va >= (int64_t)p.H * Za) continue;
+                                    const int pu = floor_div_bounded(Ua, Za, p.W);
+                                    const int pv = floor_div_bounded(Va, Za, p.H);
+                                    const uint32_t D = __ldg(A.D + pv * p.W + pu);
+                                    if constexpr (STATS) ++st_reads;
+                                    seen = Za < (((int64_t)D + 1) << 16);  // z <= D (Sec. IV-B)
+                                }
+                                if (!seen) ++c_mrg;
+                            }
+                        }
+                    }
+                }
+                if (!ray_step(r, ne, ade)) break;
+            }
+        }
+        c_abs = __reduce_add_sync(0xffffffffu, c_abs);
+        c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);
+        if constexpr (STATS) {
+            const uint32_t rays = __reduce_add_sync(0xffffffffu, (ti < p.W && tj < p.H) ? 1u : 0u);
+            st_steps = __reduce_add_sync(0xffffffffu, st_steps);
+            st_unk = __reduce_add_sync(0xffffffffu, st_unk);
+            st_anc = __reduce_add_sync(0xffffffffu, st_anc);
+            st_reads = __reduce_add_sync(0xffffffffu, st_reads);
+            if ((tid & 31) == 0) {
+                atomicAdd(p.stats + 0, (unsigned long long)rays);
+                atomicAdd(p.stats + 1, (unsigned long long)st_steps);
+                atomicAdd(p.stats + 2, (unsigned long long)st_unk);
+                atomicAdd(p.stats + 3, (unsigned long long)(uint32_t)c_abs);
+                atomicAdd(p.stats + 4, (unsigned long long)st_anc);
+                atomicAdd(p.stats + 5, (unsigned long long)st_reads);
+            }
+        }
+        if ((tid & 31) == 0 && (c_abs | c_mrg)) {
+            atomicAdd(&s_abs, c_abs);
+            atomicAdd(&s_mrg, c_mrg);
+        }
+        __syncthreads();
+        if (tid == 0 && (s_abs | s_mrg)) {
+            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2, s_abs);
+            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2 + 1, s_mrg);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------ select kernel
+// Yaw selection (Sec. III-B): lowest k with the largest marginal count (absolute count in the
+// absolute mode, where both counts are equal); g_abs = max over yaws of the absolute count.
+__global__ void select_kernel(const LevelParams p) {
+    const int l0 = p.level_off[p.lvl];
+    const int L = p.level_off[p.lvl + 1] - l0;
+    for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < L; li += gridDim.x * blockDim.x) {
+        const int n = p.level_nodes[l0 + li];
+        const int32_t *c = p.cnt + (size_t)n * p.K * 2;
+        int best = 0, bm = c[1], amax = c[0];
+        for (int k = 1; k < p.K; ++k) {
+            const int m = c[2 * k + 1];
+            if (m > bm) {
+                bm = m;
+                best = k;
+            }
+            amax = max(amax, c[2 * k]);
+        }
+        p.sel_yaw[n] = best;
+        p.out_abs[n] = amax;
+        p.out_marg[n] = bm;
+        p.out_yaw[n] = best;
+    }
+}
+
+// ------------------------------------------------------------------------------ render kernel
+// Depth buffer of the selected yaw (Sec. IV-A): per pixel ray, camera z of the entry point of
+// the first occupied voxel, else of the range endpoint. Only nodes with children (the level's
+// first level_int nodes) are rendered; descendants read them in the ancestor test.
+template <bool STATS>
+__global__ void __launch_bounds__(256) render_kernel(const LevelParams p) {
+    const int l0 = p.level_off[p.lvl];
+    const int Li = p.level_int[p.lvl];
+    const int items = Li * p.tiles;
+    const int tid = threadIdx.x;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tile = item % p.tiles;
+        const int li = item / p.tiles;
+        const int n = p.level_nodes[l0 + li];
+        const int4 nd = p.node[n];
+        if (nd.w < 0) continue;
+        const int ti = (tile % p.tiles_x) * p.tile_w + tid % p.tile_w;
+        const int tj = (tile / p.tiles_x) * p.tile_h + tid / p.tile_w;
+        if (ti >= p.W || tj >= p.H) continue;
+        const int32_t *yk = p.yawtab + p.sel_yaw[n] * 12;
+        const int4 b = p.body[tj * p.W + ti];
+        int dx, dy, dz;
+        ray_dir(b, yk[0], yk[1], dx, dy, dz);
+        RayIn r;
+        ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
+        uint32_t ne = 0, ade = 1;
+        bool hit = false;
+        uint32_t st_steps = 0;
+        for (;;) {
+            const uint8_t code = __ldg(p.grid.g + brick_addr(p.grid, r.vx, r.vy, r.vz));
+            if constexpr (STATS) ++st_steps;
+            if (code == kOcc) {
+                hit = true;
+                break;
+            }
+            if (!ray_step(r, ne, ade)) break;
+        }
+        p.arena[(size_t)nd.w * p.W * p.H + (size_t)tj * p.W + ti] = hit_depth(hit, ne, ade, b.w, p.Tq);
+        if constexpr (STATS) {
+            atomicAdd(p.stats + 6, 1ull);
+            atomicAdd(p.stats + 7, (unsigned long long)st_steps);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------- map kernels
+__global__ void map_scatter_kernel(uint8_t *bricks, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0,
+                                   int dx, int dy, int dz) {
+    const size_t total = (size_t)dx * dy * dz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % dx) + x0;
+        const int y = (int)((i / dx) % dy) + y0;
+        const int z = (int)(i / ((size_t)dx * dy)) + z0;
+        const GridView G{nullptr, 0, 0, 0, nbx, nby};
+        bricks[brick_addr(G, x, y, z)] = box[i];
+    }
+}
+
+__global__ void map_gather_kernel(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz) {
+    const size_t total = (size_t)nx * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((size_t)nx * ny));
+        const GridView G{nullptr, 0, 0, 0, nbx, nby};
+        lin[i] = bricks[brick_addr(G, x, y, z)];
+    }
+}
+
+// ----------------------------------------------------------------------------- device plan
+__global__ void plan_depth_kernel(const DevPlanParams p) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
+        int d = 0, q = p.parent[i];
+        bool bad = false;
+        if (q == -1) atomicAdd(p.roots, 1);
+        while (q != -1) {
+            if (q < 0 || q >= p.n || d >= p.max_depth) {
+                bad = true;
+                break;
+            }
+            p.anc[(size_t)i * p.max_depth + d] = q;
+            ++d;
+            q = p.parent[q];
+        }
+        if (bad) {
+            atomicOr(p.err, 1);
+            d = 0;
+        }
+        p.depth[i] = d;
+        p.anc_range[i] = make_int2(i * p.max_depth, d);
+        const int pa = p.parent[i];
+        if (!bad && pa >= 0) p.has_child[pa] = 1;
+        // quantised position, round half to even (the same IEEE double steps as the host)
+        const float pos3[3] = {p.pos[3 * (size_t)i], p.pos[3 * (size_t)i + 1], p.pos[3 * (size_t)i + 2]};
+        const float org[3] = {p.ox, p.oy, p.oz};
+        const int dims[3] = {p.nx, p.ny, p.nz};
+        int P[3];
+        for (int a = 0; a < 3; ++a) {
+            const double qd = __dmul_rn(__ddiv_rn(__dsub_rn((double)pos3[a], (double)org[a]), (double)p.voxel), 65536.0);
+            if (!(qd > -1.0 && qd < (double)dims[a] * 65536.0)) {
+                atomicOr(p.err, 2);
+                P[a] = 0;
+                continue;
+            }
+            const long long v = __double2ll_rn(qd);
+            if (v < 0 || v >= (long long)dims[a] * 65536) {
+                atomicOr(p.err, 2);
+                P[a] = 0;
+            } else {
+                P[a] = (int)v;
+            }
+        }
+        p.node[i] = make_int4(P[0], P[1], P[2], -1);
+        atomicAdd(p.level_cnt + d, 1);
+    }
+}
+
+__global__ void plan_slot_kernel(const DevPlanParams p) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
+        if (p.has_child[i]) {
+            p.node[i].w = atomicAdd(p.slot_cnt, 1);
+            atomicAdd(p.level_icnt + p.depth[i], 1);
+        }
+    }
+}
+
+__global__ void plan_scan_kernel(const DevPlanParams p) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (p.n > 0 && *p.roots != 1) atomicOr(p.err, 4);
+    const bool bad = *p.err != 0;
+    int acc = 0;
+    for (int d = 0; d <= p.max_depth; ++d) {
+        p.level_off[d] = bad ? 0 : acc;
+        p.level_int[d] = bad ? 0 : p.level_icnt[d];
+        acc += p.level_cnt[d];
+    }
+    p.level_off[p.max_depth + 1] = bad ? 0 : acc;
+    if (bad) atomicOr(p.ctx_err, *p.err);
+}
+
+__global__ void plan_scatter_kernel(const DevPlanParams p) {
+    const bool bad = *p.err != 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
+        if (bad) {
+            p.out_abs[i] = -1;
+            p.out_marg[i] = -1;
+            p.out_yaw[i] = -1;
+            continue;
+        }
+        const int d = p.depth[i];
+        int idx;
+        if (p.has_child[i]) idx = p.level_off[d] + atomicAdd(p.level_cur2 + 2 * d, 1);
+        else idx = p.level_off[d] + p.level_icnt[d] + atomicAdd(p.level_cur2 + 2 * d + 1, 1);
+        p.level_nodes[idx] = i;
+    }
+}
+
+}  // namespace
+
+void launch_count(const LevelParams &p, int grid, cudaStream_t s) {
+    if (p.stats) count_kernel<true><<<grid, p.tile_w * p.tile_h, 0, s>>>(p);
+    else count_kernel<false><<<grid, p.tile_w * p.tile_h, 0, s>>>(p);
+}
+void launch_select(const LevelParams &p, int grid, cudaStream_t s) { select_kernel<<<grid, 128, 0, s>>>(p); }
+void launch_render(const LevelParams &p, int grid, cudaStream_t s) {
+    if (p.stats) render_kernel<true><<<grid, p.tile_w * p.tile_h, 0, s>>>(p);
+    else render_kernel<false><<<grid, p.tile_w * p.tile_h, 0, s>>>(p);
+}
+void launch_map_scatter(uint8_t *bricks, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0, int dx, int dy,
+                        int dz, cudaStream_t s) {
+    const size_t total = (size_t)dx * dy * dz;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+    map_scatter_kernel<<<grid, 256, 0, s>>>(bricks, nbx, nby, box, x0, y0, z0, dx, dy, dz);
+}
+void launch_map_gather(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz, cudaStream_t s) {
+    const size_t total = (size_t)nx * ny * nz;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+    map_gather_kernel<<<grid, 256, 0, s>>>(bricks, nbx, nby, lin, nx, ny, nz);
+}
+void launch_plan(const DevPlanParams &p, cudaStream_t s) {
+    const int grid = std::max(1, std::min((p.n + 255) / 256, 1024));
+    plan_depth_kernel<<<grid, 256, 0, s>>>(p);
+    plan_slot_kernel<<<grid, 256, 0, s>>>(p);
+    plan_scan_kernel<<<1, 32, 0, s>>>(p);
+    plan_scatter_kernel<<<grid, 256, 0, s>>>(p);
+}
+
+}  // namespace mig

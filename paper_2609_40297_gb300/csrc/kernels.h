@@ -1,0 +1,73 @@
+// Device kernels of the marginal-gain path and their launch parameters (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mig {
+
+struct GridView {
+    const uint8_t *g;  // bricked codes (8x8x8 bricks of 512 B)
+    int nx, ny, nz;
+    int nbx, nby;
+};
+
+// One tree level's work (Sec. IV-C): the nodes level_nodes[level_off[lvl] ..), the first
+// level_int[lvl] of which have children and need their depth buffer rendered.
+struct LevelParams {
+    GridView grid;
+    const int4 *body;        // H*W: body-frame ray (Q30) and camera z (Q30)
+    const int32_t *yawtab;   // K*12: ck, sk, mu[3], mv[3], mz[3] (Q30, Q16)
+    int W, H, K;
+    int64_t Tq;              // range, Q16 voxel units
+    int tile_w, tile_h, tiles_x, tiles;
+    const int32_t *level_off;   // device, levels + 1
+    const int32_t *level_int;   // device, levels
+    const int32_t *level_nodes; // device, n
+    const int4 *node;           // device, n: Px, Py, Pz (Q16), arena slot
+    const int2 *anc_range;      // device, n: (offset into anc, ancestor count = depth)
+    const int32_t *anc;         // device: ancestors, parent first
+    int32_t *sel_yaw;           // device, n (written by select)
+    uint32_t *arena;            // device, slots * W * H depth buffers
+    int32_t *cnt;               // device, n*K*2 (abs, excl) counts
+    int32_t *out_abs, *out_marg, *out_yaw;  // device, n
+    int mode;                   // mig_mode
+    int lvl;
+    unsigned long long *stats;  // NULL, or 8 counters (instrumented pass)
+};
+
+void launch_count(const LevelParams &p, int grid, cudaStream_t s);
+void launch_select(const LevelParams &p, int grid, cudaStream_t s);
+void launch_render(const LevelParams &p, int grid, cudaStream_t s);
+void launch_map_scatter(uint8_t *bricks, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0, int dx, int dy,
+                        int dz, cudaStream_t s);
+void launch_map_gather(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz, cudaStream_t s);
+
+// Device planning (tree on the device): depth, levels, ancestors, slots, quantised positions.
+struct DevPlanParams {
+    int n, max_depth;
+    const int32_t *parent;
+    const float *pos;
+    float ox, oy, oz, voxel;
+    int nx, ny, nz;
+    int32_t *depth;        // n
+    int32_t *level_cnt;    // max_depth + 1 (zeroed)
+    int32_t *level_icnt;   // max_depth + 1 (zeroed)
+    int32_t *level_off;    // max_depth + 2
+    int32_t *level_int;    // max_depth + 1
+    int32_t *has_child;    // n (zeroed)
+    int32_t *level_nodes;  // n
+    int2 *anc_range;       // n: (n * max_depth, depth)
+    int32_t *anc;          // n * max_depth
+    int32_t *level_cur2;   // 2 * (max_depth + 1) (zeroed): internal / leaf scatter cursors
+    int32_t *roots;        // 1 (zeroed)
+    int4 *node;            // n
+    int32_t *slot_cnt;     // 1 (zeroed)
+    int32_t *err;          // device error word of this call
+    int32_t *ctx_err;      // context error word (read by mig_ctx_sync)
+    int32_t *out_abs, *out_marg, *out_yaw;
+};
+void launch_plan(const DevPlanParams &p, cudaStream_t s);
+
+}  // namespace mig

@@ -1,0 +1,138 @@
+// Internal declarations of the marginal-gain library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mig.h"
+
+namespace mig {
+
+constexpr int64_t kOneQ16 = 65536;
+constexpr int64_t kOneQ30 = int64_t(1) << 30;
+constexpr int kBrickShift = 3;  // 8x8x8 bricks of uint8 codes, 512 B each
+constexpr int kBrick = 1 << kBrickShift;
+constexpr int kYawRec = 12;  // per yaw: ck, sk, mu[3], mv[3], mz[3], pad
+
+// ---------------------------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+mig_status fail(mig_status st, const std::string &msg);
+#define MIG_CUDA_TRY(call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return ::mig::fail(MIG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+// ------------------------------------------------------------------------------ allocation
+struct DeviceAllocator {
+    mig_allocator user{};
+    bool has_user = false;
+    void *alloc(size_t bytes, cudaStream_t s);
+    void free(void *p, size_t bytes, cudaStream_t s);
+};
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------- camera tables
+// Per sensor: per-pixel body-frame unit rays + camera z (Q30), per-yaw rotation and projection
+// rows. Built on the host in IEEE double (no contraction), uploaded once per context.
+struct Camera {
+    mig_sensor s{};
+    int W = 0, H = 0, K = 0;
+    std::vector<int32_t> body;  // H*W*4: bx, by, bz, dzc
+    std::vector<int32_t> yaw;   // K*kYawRec
+    int32_t *d_body = nullptr;
+    int32_t *d_yaw = nullptr;
+};
+mig_status camera_build(const mig_sensor &s, Camera &out);
+mig_status sensor_check(const mig_sensor &s, float voxel);
+int64_t range_q16(float range_m, float voxel);
+
+// ------------------------------------------------------------------------------------- plan
+struct HostPlan {
+    int n = 0, max_depth = 0, n_internal = 0, total_anc = 0;
+    std::vector<int32_t> depth;       // n
+    std::vector<int32_t> level_off;   // max_depth + 2
+    std::vector<int32_t> level_int;   // max_depth + 1: internal nodes leading each level
+    std::vector<int32_t> level_nodes; // n (internal nodes first within a level)
+    std::vector<int32_t> anc_off;     // n + 1
+    std::vector<int32_t> anc;         // ancestors, parent first
+    std::vector<int32_t> node;        // n*4: Px, Py, Pz (Q16), slot (-1 = leaf)
+};
+mig_status tree_check(int n, const int32_t *parent, int32_t *depth, int32_t *max_depth);
+mig_status plan_build(int n, const int32_t *parent, const float *pos, const float origin[3], float voxel,
+                      const int dims[3], HostPlan &p);
+
+// CUDA-event timing of the library's own launches (mig_ctx_profile).
+enum ProfKind { kProfCount = 0, kProfSelect, kProfRender, kProfPlan, kProfBatch, kProfKinds };
+struct Profiler {
+    bool on = false;
+    struct Pair {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pair> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[kProfKinds] = {0, 0, 0, 0, 0};
+    uint64_t launches[kProfKinds] = {0, 0, 0, 0, 0};
+};
+
+}  // namespace mig
+
+// ----------------------------------------------------------------------------- public objects
+struct mig_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mig::DeviceAllocator alloc;
+    int num_sms = 0;
+    std::vector<std::unique_ptr<mig::Camera>> cameras;
+    mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
+    void *pinned = nullptr;  // pinned host staging
+    size_t pinned_bytes = 0;
+    int32_t *d_err = nullptr;  // device-side check word (device planning)
+    mig_tile_config tiles{16, 16, 4};
+    mig::Profiler prof;
+    struct Batch;            // batched engine state (batch.cu)
+    Batch *batch = nullptr;
+    std::mutex mu;           // serialises calls that share the workspace
+};
+
+struct mig_map {
+    mig_ctx *ctx = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    int nbx = 0, nby = 0, nbz = 0;  // bricks per axis
+    float voxel = 0.f;
+    float origin[3] = {0.f, 0.f, 0.f};
+    uint8_t *d_grid = nullptr;       // bricked codes, nbx*nby*nbz*512 bytes
+    size_t grid_bytes = 0;
+    uint64_t version = 0;
+};
+
+namespace mig {
+// workspace / staging helpers (api.cu)
+mig_status ctx_workspace(mig_ctx *ctx, size_t bytes, void **out);
+mig_status ctx_pinned(mig_ctx *ctx, size_t bytes, void **out);
+mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out);
+// records an event pair around launch() on the context stream when profiling is on
+void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a);
+void prof_end(mig_ctx *ctx, int kind, cudaEvent_t a);
+template <class F>
+inline void timed_launch(mig_ctx *ctx, int kind, F &&launch) {
+    cudaEvent_t a = nullptr;
+    prof_begin(ctx, kind, &a);
+    launch();
+    prof_end(ctx, kind, a);
+}
+}  // namespace mig

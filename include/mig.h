@@ -148,6 +148,26 @@ mig_status mig_tree_eval_device(mig_map *map, int n, const int32_t *parent, cons
                                 int32_t *best_yaw);
 
 /* ---------------------------------------------------------------------------------------
+ * Allocation-free evaluation. The paper has no counterpart; this entry point serves callers
+ * that may not allocate device memory: a planner in a real-time control loop whose policy
+ * forbids cudaMalloc after start-up (an allocation can stall or synchronise the device for an
+ * unbounded time), or a host framework that owns all device memory through its own pool.
+ * Same arguments, device pointers, asynchrony and device-side checks as mig_tree_eval_device,
+ * and the same results. It calls no cudaMalloc, cudaFree or other allocating routine: all
+ * scratch (camera tables, plan, counters, depth buffers) lives in one static device array of
+ * MIG_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until the process exits.
+ * A tree needs about n * width * height * 4 bytes plus n * (K * 8 + 64 + 4 * max_depth) bytes;
+ * a larger request returns MIG_EINVAL with the size in mig_last_error. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Every call shares the one array: calls whose work overlaps on
+ * the GPU (other streams, other contexts on the same device) race and corrupt each other.
+ * --------------------------------------------------------------------------------------- */
+#define MIG_NOALLOC_SCRATCH_BYTES (64u << 20)
+mig_status mig_tree_eval_device_noalloc(mig_map *map, int n, const int32_t *parent, const float *pos_m,
+                                        const mig_sensor *sensor, int max_depth, int32_t *abs_gain,
+                                        int32_t *marg_gain, int32_t *best_yaw);
+
+/* ---------------------------------------------------------------------------------------
  * Batched evaluation: many independent trees (each on its own map and sensor) in one
  * persistent launch with per-level device work queues, replayed from a captured CUDA graph
  * when the batch's shape repeats. Host arrays as in mig_tree_eval; results are identical to

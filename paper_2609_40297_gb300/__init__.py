@@ -29,7 +29,7 @@ EXPORTS = [
     "mig_ctx_create", "mig_ctx_destroy", "mig_ctx_set_stream", "mig_ctx_sync",
     "mig_map_create", "mig_map_update", "mig_map_read", "mig_map_destroy",
     "mig_default_resolution", "mig_tree_check",
-    "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device",
+    "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device", "mig_tree_eval_device_noalloc",
     "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles",
     "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
 ]
@@ -123,6 +123,7 @@ def lib():
                 "mig_tree_eval": (st, [p, i, p, p, p, p, p, p]),
                 "mig_tree_eval_ex": (st, [p, i, p, p, p, p, p, p, p]),
                 "mig_tree_eval_device": (st, [p, i, p, p, p, i, p, p, p]),
+                "mig_tree_eval_device_noalloc": (st, [p, i, p, p, p, i, p, p, p]),
                 "mig_tree_eval_batch": (st, [p, i, p]),
                 "mig_batch_set_tiles": (st, [p, p]),
                 "mig_batch_get_tiles": (st, [p, p]),
@@ -315,6 +316,17 @@ def tree_eval_device(m: Map, parent_dev, pos_dev, sensor, max_depth, abs_dev, ma
     check(lib().mig_tree_eval_device(m.h, n, C.c_void_p(parent_dev.data_ptr()), C.c_void_p(pos_dev.data_ptr()),
                                      C.byref(s), int(max_depth), C.c_void_p(abs_dev.data_ptr()),
                                      C.c_void_p(marg_dev.data_ptr()), C.c_void_p(yaw_dev.data_ptr())))
+
+
+def tree_eval_device_noalloc(m: Map, parent_dev, pos_dev, sensor, max_depth, abs_dev, marg_dev, yaw_dev):
+    """mig_tree_eval_device_noalloc: as tree_eval_device, with all scratch in the library's static
+    device array (nothing is allocated); calls that overlap on the GPU race."""
+    n = int(parent_dev.shape[0])
+    s = Sensor.of(sensor)
+    check(lib().mig_tree_eval_device_noalloc(m.h, n, C.c_void_p(parent_dev.data_ptr()),
+                                             C.c_void_p(pos_dev.data_ptr()), C.byref(s), int(max_depth),
+                                             C.c_void_p(abs_dev.data_ptr()), C.c_void_p(marg_dev.data_ptr()),
+                                             C.c_void_p(yaw_dev.data_ptr())))
 
 
 def tree_eval_batch(ctx: Context, problems, maps, mode=MODE_MARGINAL):

@@ -298,7 +298,7 @@ def cpu_baseline(workload, sample_depth=None, budget_s=20.0):
     s = prob.sensor
     d = prob.tree.depth()
     if sample_depth is None:
-        sample_depth = {"tiny": 10, "paper_scale": 5, "large": 1}.get(workload, 3)
+        sample_depth = {"tiny": 10, "paper_scale": 10, "large": 2}.get(workload, 3)
     mask = (d <= sample_depth).astype(np.uint8)
     m = int(mask.sum())
     t0 = time.perf_counter()

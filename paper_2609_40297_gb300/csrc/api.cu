@@ -206,6 +206,7 @@ mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocat
         ctx->alloc.has_user = true;
     }
     MIG_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+    ctx->count_ctas = count_ctas_per_sm();
     ctx->d_err = (int32_t *)ctx->alloc.alloc(256, ctx->stream);
     if (!ctx->d_err) return fail(MIG_ENOMEM, "ctx_create: allocation failed");
     MIG_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream));
@@ -311,10 +312,7 @@ mig_status mig_map_create(mig_ctx *ctx, int nx, int ny, int nz, float voxel_size
     m->nx = nx;
     m->ny = ny;
     m->nz = nz;
-    m->nbx = (nx + kBrick - 1) / kBrick;
-    m->nby = (ny + kBrick - 1) / kBrick;
-    m->nbz = (nz + kBrick - 1) / kBrick;
-    m->grid_bytes = (size_t)m->nbx * m->nby * m->nbz * 512;
+    m->grid_bytes = map_layout_bytes(nx, ny, nz, &m->nbx, &m->nby, &m->nbz);
     if (m->grid_bytes >= ((size_t)1 << 32)) return fail(MIG_EINVAL, "map_create: padded grid above 2^32 voxels");
     m->voxel = voxel_size_m;
     for (int a = 0; a < 3; ++a) m->origin[a] = origin_m ? origin_m[a] : 0.f;
@@ -335,7 +333,7 @@ mig_status mig_map_create(mig_ctx *ctx, int nx, int ny, int nz, float voxel_size
             return fail(MIG_ENOMEM, "map_create: staging allocation failed");
         }
         MIG_CUDA_TRY(cudaMemcpyAsync(tmp, host_voxels, nvox, cudaMemcpyHostToDevice, ctx->stream));
-        launch_map_scatter(m->d_grid, m->nbx, m->nby, tmp, 0, 0, 0, nx, ny, nz, ctx->stream);
+        launch_map_scatter(m->d_grid, m->nx, m->ny, m->nbx, m->nby, tmp, 0, 0, 0, nx, ny, nz, ctx->stream);
         MIG_CUDA_TRY(cudaGetLastError());
         ctx->alloc.free(tmp, nvox, ctx->stream);
     }
@@ -357,7 +355,7 @@ mig_status mig_map_update(mig_map *m, int x0, int y0, int z0, int dx, int dy, in
     uint8_t *tmp = (uint8_t *)ctx->alloc.alloc(nvox, ctx->stream);
     if (!tmp) return fail(MIG_ENOMEM, "map_update: staging allocation failed");
     MIG_CUDA_TRY(cudaMemcpyAsync(tmp, host_voxels, nvox, cudaMemcpyHostToDevice, ctx->stream));
-    launch_map_scatter(m->d_grid, m->nbx, m->nby, tmp, x0, y0, z0, dx, dy, dz, ctx->stream);
+    launch_map_scatter(m->d_grid, m->nx, m->ny, m->nbx, m->nby, tmp, x0, y0, z0, dx, dy, dz, ctx->stream);
     MIG_CUDA_TRY(cudaGetLastError());
     ctx->alloc.free(tmp, nvox, ctx->stream);
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // the host buffer may be reused on return
@@ -450,6 +448,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     const size_t up_bytes = cv.off;
     const size_t o_sel = cv.take<int32_t>(n), o_out = cv.take<int32_t>(3 * (size_t)n);
     const size_t o_cnt = cv.take<int32_t>((size_t)n * K * 2);
+    const size_t o_work = cv.take<int32_t>(L);
     const size_t o_arena = cv.take<uint32_t>((size_t)std::max(1, plan.n_internal) * WH);
     const size_t o_stats = cv.take<unsigned long long>(8);
     char *dev = nullptr;
@@ -470,7 +469,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         std::memcpy(host + o_lnodes, plan.level_nodes.data(), (size_t)n * 4);
     }
     MIG_CUDA_TRY(cudaMemcpyAsync(dev, host, up_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    MIG_CUDA_TRY(cudaMemsetAsync(dev + o_cnt, 0, (size_t)n * K * 2 * 4, ctx->stream));
+    MIG_CUDA_TRY(cudaMemsetAsync(dev + o_cnt, 0, o_arena - o_cnt, ctx->stream));  // counters + work counters
     LevelParams p = level_params(m, cam, ctx);
     p.level_off = (const int32_t *)(dev + o_loff);
     p.level_int = (const int32_t *)(dev + o_lint);
@@ -483,6 +482,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.out_marg = p.out_abs + n;
     p.out_yaw = p.out_abs + 2 * (size_t)n;
     p.cnt = (int32_t *)(dev + o_cnt);
+    p.work = (int32_t *)(dev + o_work);
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = mode;
     if (stats) {
@@ -490,15 +490,17 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
     }
     const int cap = ctx->num_sms * 16;
+    const int count_cap = ctx->num_sms * ctx->count_ctas;
     uint64_t n_count = 0, n_render = 0;
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
         const int Ld = plan.level_off[d + 1] - plan.level_off[d];
         const int items = Ld * K * p.tiles;
-        timed_launch(ctx, kProfCount, [&] { launch_count(p, std::max(1, std::min(items, cap)), ctx->stream); });
+        const int cgrid = std::max(1, std::min((items + 7) / 8, count_cap));
+        timed_launch(ctx, kProfCount, [&] { launch_count(p, cgrid, ctx->stream); });
         timed_launch(ctx, kProfSelect,
                      [&] { launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), ctx->stream); });
-        const int ritems = plan.level_int[d] * p.tiles;
+        const int ritems = plan.level_int[d] * render_tiles(p.W, p.H);
         if (ritems > 0) timed_launch(ctx, kProfRender, [&] { launch_render(p, std::min(ritems, cap), ctx->stream); });
         n_count++;
         n_render += ritems > 0;
@@ -578,6 +580,7 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     const size_t o_lcnt = cv.take<int32_t>(L), o_licnt = cv.take<int32_t>(L), o_cur2 = cv.take<int32_t>(2 * L);
     const size_t o_hasc = cv.take<int32_t>(n), o_slot = cv.take<int32_t>(1), o_roots = cv.take<int32_t>(1);
     const size_t o_err = cv.take<int32_t>(1), o_cnt = cv.take<int32_t>((size_t)n * K * 2);
+    const size_t o_work = cv.take<int32_t>(L);
     const size_t zero_bytes = cv.off;
     const size_t o_depth = cv.take<int32_t>(n), o_loff = cv.take<int32_t>(L + 1), o_lint = cv.take<int32_t>(L);
     const size_t o_lnodes = cv.take<int32_t>(n), o_ar = cv.take<int2>(n);
@@ -631,13 +634,15 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     p.out_marg = marg_gain;
     p.out_yaw = best_yaw;
     p.cnt = (int32_t *)(dev + o_cnt);
+    p.work = (int32_t *)(dev + o_work);
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
     const int cap = ctx->num_sms * 16;
+    const int count_cap = ctx->num_sms * ctx->count_ctas;
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
-        timed_launch(ctx, kProfCount, [&] { launch_count(p, cap, ctx->stream); });
+        timed_launch(ctx, kProfCount, [&] { launch_count(p, count_cap, ctx->stream); });
         timed_launch(ctx, kProfSelect, [&] { launch_select(p, sel_grid, ctx->stream); });
         timed_launch(ctx, kProfRender, [&] { launch_render(p, cap, ctx->stream); });
     }

@@ -22,9 +22,9 @@ extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_t
 
 extern "C" mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg) {
     if (!ctx || !cfg) return mig::fail(MIG_EINVAL, "batch_set_tiles: NULL argument");
-    if (cfg->tile_w < 1 || cfg->tile_h < 1 || cfg->tile_w * cfg->tile_h > 256 || (cfg->tile_w * cfg->tile_h) % 32 != 0 ||
+    if (cfg->tile_w < 1 || cfg->tile_h < 1 || cfg->tile_w * cfg->tile_h > 4096 || (cfg->tile_w * cfg->tile_h) % 32 != 0 ||
         cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 32)
-        return mig::fail(MIG_EINVAL, "batch_set_tiles: tile must have a multiple of 32 threads, at most 256");
+        return mig::fail(MIG_EINVAL, "batch_set_tiles: a tile holds a multiple of 32 rays, at most 4096");
     ctx->tiles = *cfg;
     return MIG_OK;
 }

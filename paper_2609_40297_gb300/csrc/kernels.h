@@ -8,7 +8,7 @@
 namespace mig {
 
 struct GridView {
-    const uint8_t *g;  // bricked codes (8x8x8 bricks of 512 B)
+    const uint8_t *g;  // voxel codes in the traversal layout (x-fastest rows or 8x8x8 bricks)
     int nx, ny, nz;
     int nbx, nby;
 };
@@ -21,7 +21,7 @@ struct LevelParams {
     const int32_t *yawtab;   // K*12: ck, sk, mu[3], mv[3], mz[3] (Q30, Q16)
     int W, H, K;
     int64_t Tq;              // range, Q16 voxel units
-    int tile_w, tile_h, tiles_x, tiles;
+    int tile_w, tile_h, tiles_x, tiles;  // count-pass tile (rays per warp work item)
     const int32_t *level_off;   // device, levels + 1
     const int32_t *level_int;   // device, levels
     const int32_t *level_nodes; // device, n
@@ -31,6 +31,7 @@ struct LevelParams {
     int32_t *sel_yaw;           // device, n (written by select)
     uint32_t *arena;            // device, slots * W * H depth buffers
     int32_t *cnt;               // device, n*K*2 (abs, excl) counts
+    int32_t *work;              // device, levels: count-pass work counters (zeroed)
     int32_t *out_abs, *out_marg, *out_yaw;  // device, n
     int mode;                   // mig_mode
     int lvl;
@@ -38,10 +39,14 @@ struct LevelParams {
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);
+int count_ctas_per_sm();  // resident CTAs per SM of the count kernel
 void launch_select(const LevelParams &p, int grid, cudaStream_t s);
 void launch_render(const LevelParams &p, int grid, cudaStream_t s);
-void launch_map_scatter(uint8_t *bricks, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0, int dx, int dy,
-                        int dz, cudaStream_t s);
+int render_tiles(int W, int H);  // 16x16 pixel tiles of the render pass
+void launch_map_scatter(uint8_t *bricks, int nx, int ny, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0,
+                        int dx, int dy, int dz, cudaStream_t s);
+// device bytes of an nx*ny*nz grid in the traversal layout (and its brick counts)
+size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz);
 void launch_map_gather(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz, cudaStream_t s);
 
 // Device planning (tree on the device): depth, levels, ancestors, slots, quantised positions.

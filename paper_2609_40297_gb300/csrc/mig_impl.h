@@ -97,12 +97,13 @@ struct mig_ctx {
     cudaStream_t stream = nullptr;
     mig::DeviceAllocator alloc;
     int num_sms = 0;
+    int count_ctas = 1;        // resident count-kernel CTAs per SM
     std::vector<std::unique_ptr<mig::Camera>> cameras;
     mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
     void *pinned = nullptr;  // pinned host staging
     size_t pinned_bytes = 0;
     int32_t *d_err = nullptr;  // device-side check word (device planning)
-    mig_tile_config tiles{16, 16, 4};
+    mig_tile_config tiles{4, 16, 4};  // count-pass tile: 64 rays per warp work item
     mig::Profiler prof;
     struct Batch;            // batched engine state (batch.cu)
     Batch *batch = nullptr;

@@ -93,6 +93,7 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     const size_t o_lcnt = cv.take(4 * (size_t)L), o_licnt = cv.take(4 * (size_t)L), o_cur2 = cv.take(8 * (size_t)L);
     const size_t o_hasc = cv.take(4 * (size_t)n), o_slot = cv.take(4), o_roots = cv.take(4), o_err = cv.take(4);
     const size_t o_cnt = cv.take(8 * (size_t)n * K);
+    const size_t o_work = cv.take(4 * (size_t)L);
     const size_t zero_bytes = cv.off;
     const size_t o_depth = cv.take(4 * (size_t)n), o_loff = cv.take(4 * (size_t)(L + 1)), o_lint = cv.take(4 * (size_t)L);
     const size_t o_lnodes = cv.take(4 * (size_t)n), o_ar = cv.take(8 * (size_t)n);
@@ -200,6 +201,7 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     p.out_marg = marg_gain;
     p.out_yaw = best_yaw;
     p.cnt = (int32_t *)(dev + o_cnt);
+    p.work = (int32_t *)(dev + o_work);
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
     p.stats = nullptr;
@@ -207,7 +209,7 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
-        launch_count(p, cap, s);
+        launch_count(p, ctx->num_sms * ctx->count_ctas, s);
         launch_select(p, sel_grid, s);
         launch_render(p, cap, s);
     }

@@ -35,7 +35,7 @@ def run_both(ctx, grid, voxel, origin, parent, pos, sensor, mode=0, depth=True, 
     finally:
         m.close()
         if tiles:
-            ctx.set_tiles(16, 16, 4)
+            ctx.set_tiles(4, 16, 4)
     ref = oracle.eval_tree(grid, voxel, origin, parent, pos, sensor, mode=mode, want_counts=True, want_depth=depth)
     return got, ref
 
@@ -80,7 +80,7 @@ def test_sensors_bit_exact(ctx, sensor):
     assert_same(got, ref)
 
 
-@pytest.mark.parametrize("tiles", [(32, 8, 4), (8, 4, 8), (16, 2, 4), (32, 1, 8)])
+@pytest.mark.parametrize("tiles", [(32, 8, 4), (8, 4, 8), (16, 2, 4), (32, 1, 8), (8, 8, 4), (16, 64, 4)])
 def test_tile_shapes_bit_exact(ctx, tiles):
     p = synth.random_small(31, n_nodes=18, max_depth=6)
     got, ref = run_both(ctx, p.map.grid, p.map.voxel_size, p.map.origin, p.tree.parent, p.tree.pos, p.sensor,

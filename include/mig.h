@@ -190,11 +190,32 @@ mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_tree_desc *t
 
 /* Tile shape of the batched kernel (chosen by the autotuner; exposed for the tuner and tests). */
 typedef struct mig_tile_config {
-    int32_t tile_w, tile_h;   /* pixels per work item (tile_w * tile_h threads per CTA) */
+    int32_t tile_w, tile_h;   /* count pass: pixel rays per warp work item (a multiple of 32, <= 4096) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM */
+    int32_t engine;           /* batches: 0 = one persistent dataflow kernel, 1 = per-tree launch
+                                 chains on concurrent streams in one graph */
 } mig_tile_config;
 mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg);
 mig_status mig_batch_get_tiles(mig_ctx *ctx, mig_tile_config *cfg);
+/* Time limit of every device-side dependency wait of the batched kernel (default 5 s); after
+ * it the launch stops and returns MIG_ETIMEOUT, leaving the context usable. debug_stall != 0 is
+ * a test hook that makes one level of the next batches never complete, so that the waits
+ * behind it run out. */
+mig_status mig_batch_set_timeout(mig_ctx *ctx, int64_t timeout_us, int debug_stall);
+/* Number of CUDA-graph captures and replays of batched launches so far (a batch of the same
+ * shape as the previous one replays the captured graph; the legacy default stream and
+ * profiling use plain launches). */
+mig_status mig_batch_graph_stats(mig_ctx *ctx, uint64_t *captures, uint64_t *replays);
+/* Device-side trace of batched launches: with tracing on, every segment (the count or the render
+ * work of one tree level) records when it became ready and when its last item finished
+ * (microseconds from the kernel start, %globaltimer). mig_batch_trace_read copies the records of
+ * the last traced launch (n = number available). Traced launches do not use the graph. */
+typedef struct mig_trace_rec {
+    int32_t tree, level, phase, items; /* phase 0 = count, 1 = render */
+    double activated_us, done_us;
+} mig_trace_rec;
+mig_status mig_batch_trace(mig_ctx *ctx, int enable);
+mig_status mig_batch_trace_read(mig_ctx *ctx, mig_trace_rec *out, int cap, int *n);
 
 
 /* ---------------------------------------------------------------------------------------

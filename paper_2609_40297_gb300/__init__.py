@@ -30,7 +30,8 @@ EXPORTS = [
     "mig_map_create", "mig_map_update", "mig_map_read", "mig_map_destroy",
     "mig_default_resolution", "mig_tree_check",
     "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device", "mig_tree_eval_device_noalloc",
-    "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles",
+    "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles", "mig_batch_set_timeout",
+    "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read",
     "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
 ]
 
@@ -83,8 +84,13 @@ class EvalStats(C.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class TraceRec(C.Structure):
+    _fields_ = [("tree", C.c_int32), ("level", C.c_int32), ("phase", C.c_int32), ("items", C.c_int32),
+                ("activated_us", C.c_double), ("done_us", C.c_double)]
+
+
 class TileConfig(C.Structure):
-    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("ctas_per_sm", C.c_int32)]
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("ctas_per_sm", C.c_int32), ("engine", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -127,6 +133,10 @@ def lib():
                 "mig_tree_eval_batch": (st, [p, i, p]),
                 "mig_batch_set_tiles": (st, [p, p]),
                 "mig_batch_get_tiles": (st, [p, p]),
+                "mig_batch_set_timeout": (st, [p, C.c_int64, i]),
+                "mig_batch_graph_stats": (st, [p, p, p]),
+                "mig_batch_trace": (st, [p, i]),
+                "mig_batch_trace_read": (st, [p, p, i, p]),
                 "mig_server_create": (st, [p, C.c_size_t, i, p]),
                 "mig_server_submit": (st, [p, p, p]),
                 "mig_server_poll": (st, [p, C.c_uint64, C.c_int64]),
@@ -199,13 +209,33 @@ class Context:
     def sync(self):
         check(lib().mig_ctx_sync(self.h))
 
-    def set_tiles(self, tile_w, tile_h, ctas_per_sm=4):
-        check(lib().mig_batch_set_tiles(self.h, C.byref(TileConfig(tile_w, tile_h, ctas_per_sm))))
+    def set_tiles(self, tile_w, tile_h, ctas_per_sm=4, engine=None):
+        if engine is None:
+            engine = self.get_tiles()[3]
+        check(lib().mig_batch_set_tiles(self.h, C.byref(TileConfig(tile_w, tile_h, ctas_per_sm, engine))))
+
+    def set_batch_timeout(self, timeout_us, debug_stall=False):
+        check(lib().mig_batch_set_timeout(self.h, int(timeout_us), 1 if debug_stall else 0))
+
+    def graph_stats(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        check(lib().mig_batch_graph_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def batch_trace(self, enable=True):
+        check(lib().mig_batch_trace(self.h, 1 if enable else 0))
+
+    def batch_trace_read(self):
+        n = C.c_int()
+        check(lib().mig_batch_trace_read(self.h, None, 0, C.byref(n)))
+        recs = (TraceRec * max(1, n.value))()
+        check(lib().mig_batch_trace_read(self.h, recs, n.value, C.byref(n)))
+        return [{f: getattr(r, f) for f, _ in TraceRec._fields_} for r in recs[:n.value]]
 
     def get_tiles(self):
         t = TileConfig()
         check(lib().mig_batch_get_tiles(self.h, C.byref(t)))
-        return (t.tile_w, t.tile_h, t.ctas_per_sm)
+        return (t.tile_w, t.tile_h, t.ctas_per_sm, t.engine)
 
     def profile(self, enable=True):
         check(lib().mig_ctx_profile(self.h, 1 if enable else 0))

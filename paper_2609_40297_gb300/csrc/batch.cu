@@ -1,36 +1,806 @@
-// Batched evaluation of many independent trees (placeholder: sequential per-tree evaluation).
-#include "mig_impl.h"
+// Batched evaluation of many independent trees in one persistent launch (Sec. IV-C per tree).
+//
+// Work items are ordered level-major over all trees: for level d, the count items (node, yaw,
+// tile) of every tree that has a level d, then the render items (internal node, 32 pixels) of
+// those trees. Warps take items from one atomic counter. A count item of tree t at level d
+// waits until level d-1 of tree t is complete (its depth buffers are written); the warp that
+// finishes the last count item of (t, d) performs the yaw selection of the level; a render item
+// waits for that selection. Every wait is bounded by a time limit; a wait that runs out sets an
+// abort flag, all warps leave, and the host returns MIG_ETIMEOUT.
+//
+// The host packs the plans of all trees into one upload, launches the persistent kernel and
+// downloads all outputs; the sequence is captured once into a CUDA graph and replayed while the
+// batch keeps the same shape.
+#include <cuda/atomic>
+#include <cuda_runtime.h>
 
-struct mig_ctx::Batch {};
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <memory>
+
+#include "batch.h"
+#include "dev_path.cuh"
+#include "kernels.h"
+
+namespace mig {
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int *p) {
+    return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_acquire);
+}
+
+__device__ __forceinline__ int load_relaxed_i(const int *p) {
+    return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ unsigned long long load_relaxed_u64(const unsigned long long *p) {
+    return cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device>(*p).load(cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ void store_release(int *p, int v) {
+    cuda::atomic_ref<int, cuda::thread_scope_device>(*p).store(v, cuda::memory_order_release);
+}
+
+constexpr unsigned long long kActItemsMask = (1ull << 40) - 1;
+
+// Appends a ready segment to the activation log and gives it the next item numbers.
+__device__ void activate(const BatchParams &bp, int seg) {
+    const int items = bp.segs[seg].items;
+    if (bp.trace) bp.trace[2 * (size_t)seg] = global_ns();
+    const unsigned long long old = atomicAdd(bp.act, (1ull << 40) | (unsigned long long)items);
+    const int pos = (int)(old >> 40);
+    bp.log[pos] = make_int2((int)(old & kActItemsMask), seg);
+    __threadfence();
+    store_release(bp.log_valid + pos, 1);
+}
+
+// Level (tree, level) is complete: its depth buffers are written; its next level becomes ready.
+__device__ void level_done(const BatchParams &bp, const BatchTree &T, int tree, int level) {
+    const int next = level + 1;
+    if (next < T.n_levels && bp.segs[2 * (T.lvl_base + next)].items > 0) activate(bp, 2 * (T.lvl_base + next));
+    (void)tree;
+}
+
+__device__ __forceinline__ bool timed_out(const BatchParams &bp, unsigned long long &deadline) {
+    if (deadline == 0) deadline = global_ns() + bp.timeout_ns;
+    if (global_ns() > deadline) {
+        atomicExch(bp.status + 1, 1);
+        atomicExch(bp.status, 1);
+        return true;
+    }
+    return false;
+}
+
+#ifndef MIG_BATCH_MINB
+#define MIG_BATCH_MINB MIG_COUNT_MINB
+#endif
+__global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(const BatchParams bp) {
+    __shared__ AncRec s_anc[kWarps][MIG_MAX_DEPTH];
+    __shared__ unsigned long long s_q[kWarps][64];
+    __shared__ int4 s_cam[kWarps][4];
+    __shared__ HotVals s_hot[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (bp.trace && blockIdx.x == 0 && threadIdx.x == 0) bp.trace[2 * (size_t)bp.n_segs_total] = global_ns();
+    int pos = 0;  // (lane 0) activation-log entry of this warp's previous item (entries only grow)
+    int cur_tree = -1;  // tree whose loop-live parameters s_hot[warp] holds
+    for (;;) {
+        // lane 0 takes the next item number, waits (bounded) until it is activated, finds its
+        // activation-log entry with relaxed loads, then one acquire fence orders this warp's
+        // reads after the dependencies' writes; the result is broadcast to the warp
+        int seg = -1, local = 0;
+        if (lane == 0) {
+            const long long g = load_relaxed_i(bp.status) ? LLONG_MAX
+                                                          : (long long)atomicAdd((unsigned long long *)bp.work, 1ull);
+            if (g < bp.total_items) {
+                unsigned long long deadline = 0, a = 0;
+                bool ok = true;
+                unsigned nap = 128;  // exponential backoff keeps idle warps off the memory system
+                for (;;) {
+                    a = load_relaxed_u64(bp.act);
+                    if ((long long)(a & kActItemsMask) > g) break;
+                    if (load_relaxed_i(bp.status) || timed_out(bp, deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(nap);
+                    nap = min(nap * 2, 8192u);
+                }
+                int lo = pos, hi = (int)(a >> 40) - 1;
+                while (ok && lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    while (!load_relaxed_i(bp.log_valid + mid))
+                        if (load_relaxed_i(bp.status) || timed_out(bp, deadline)) {
+                            ok = false;
+                            break;
+                        }
+                    if (ok) {
+                        if ((long long)load_relaxed_i(&bp.log[mid].x) <= g) lo = mid;
+                        else hi = mid - 1;
+                    }
+                }
+                while (ok && !load_relaxed_i(bp.log_valid + lo))
+                    if (load_relaxed_i(bp.status) || timed_out(bp, deadline)) ok = false;
+                if (ok) {
+                    cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+                    pos = lo;
+                    seg = load_relaxed_i(&bp.log[lo].y);
+                    local = (int)(g - load_relaxed_i(&bp.log[lo].x));
+                } else {
+                    seg = -2;
+                }
+            }
+        }
+        seg = __shfl_sync(0xffffffffu, seg, 0);
+        local = __shfl_sync(0xffffffffu, local, 0);
+        __syncwarp();
+        if (seg < 0) break;
+        const int2 e = make_int2(0, seg);
+        const SegInfo sg = bp.segs[e.y];
+        const BatchTree &T = bp.trees[sg.tree];
+        const LevelParams &p = T.p;
+        const int idx = T.lvl_base + sg.level;
+        const int l0 = p.level_off[sg.level];
+        if (!sg.render) {
+            if (sg.tree != cur_tree) {
+                if (lane == 0) {
+                    HotVals h;
+                    h.g = p.grid.g;
+                    h.body = p.body;
+                    h.yawtab = p.yawtab;
+                    h.Tq = p.Tq;
+                    h.nx = p.grid.nx;
+                    h.ny = p.grid.ny;
+                    h.nz = p.grid.nz;
+                    h.W = p.W;
+                    h.H = p.H;
+                    h.tile_w = p.tile_w;
+                    h.pad0 = h.pad1 = 0;
+                    s_hot[warp] = h;
+                }
+                __syncwarp();
+                cur_tree = sg.tree;
+            }
+            count_chunk<false>(p, HotStaged{&s_hot[warp]}, l0, local, s_anc[warp], s_q[warp], s_cam[warp], lane);
+            int last = 0;
+            if (lane == 0) {
+                __threadfence();
+                last = atomicSub(bp.count_left + idx, 1) == 1;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {  // every count item of (tree, level) is done: select the yaws
+                if (bp.trace && lane == 0) bp.trace[2 * (size_t)e.y + 1] = global_ns();
+                __threadfence();
+                const int L = p.level_off[sg.level + 1] - l0;
+                for (int i = lane; i < L; i += 32) select_node(p, p.level_nodes[l0 + i]);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    if (bp.segs[e.y + 1].items > 0) activate(bp, e.y + 1);
+                    else level_done(bp, T, sg.tree, sg.level);
+                }
+            }
+        } else {
+            const int WH = p.W * p.H;
+            const int groups = (WH + 31) >> 5;
+            const int li = local / groups;
+            const int pix = (local - li * groups) * 32 + lane;
+            if (pix < WH) {
+                const int n = p.level_nodes[l0 + li];
+                render_pixel(p, n, p.node[n], pix % p.W, pix / p.W);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                if (atomicSub(bp.render_left + idx, 1) == 1) {
+                    if (bp.trace) bp.trace[2 * (size_t)e.y + 1] = global_ns();
+                    __threadfence();
+                    level_done(bp, T, sg.tree, sg.level);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void launch_batch(const BatchParams &bp, int grid, cudaStream_t s) { batch_kernel<<<grid, kWarps * 32, 0, s>>>(bp); }
+
+int batch_ctas_per_sm() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kWarps * 32, 0);
+    cudaGetLastError();
+    return std::max(1, a);
+}
+
+}  // namespace mig
+
+using namespace mig;
+
+namespace {
+struct GraphKey {
+    BatchParams bp;
+    void *host;
+    size_t up, zero_start, zero, down_start, down, status;
+    int grid;
+};
+}  // namespace
+
+struct mig_ctx::Batch {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    GraphKey key;  // shape of the captured graph
+    int ctas = 0;
+    uint64_t replays = 0, captures = 0;
+    std::vector<mig_trace_rec> trace;  // last traced launch
+    // stream-chain engine: stream pool, fork/join events, its own captured graph
+    static constexpr size_t kPool = 16;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    cudaGraph_t sgraph = nullptr;
+    std::vector<char> skey;
+    Batch() { std::memset(&key, 0, sizeof(key)); }
+};
+
+namespace {
+
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
+    const int T = (int)items.size();
+    if (T > kBatchMaxTrees) return fail(MIG_EINVAL, "batch_run: too many trees for one launch");
+    // ---- segments: per (tree, level) a count and a render segment; those outside a tree's
+    // launch range [level_lo, level_hi] have no items
+    int total_levels = 0;
+    std::vector<int> lvl_base(T);
+    for (int t = 0; t < T; ++t) {
+        lvl_base[t] = total_levels;
+        total_levels += items[t].plan.max_depth + 1;
+    }
+    const mig_tile_config tc = ctx->tiles;
+    std::vector<int> tiles_count(T), groups(T);
+    std::vector<SegInfo> segs(2 * (size_t)total_levels);
+    std::vector<int> cnt_left(total_levels, 0), rnd_left(total_levels, 0);
+    long long total = 0;
+    int n_nonempty = 0;
+    for (int t = 0; t < T; ++t) {
+        const BatchItem &it = items[t];
+        const int W = it.cam->W, H = it.cam->H;
+        tiles_count[t] = ((W + tc.tile_w - 1) / tc.tile_w) * ((H + tc.tile_h - 1) / tc.tile_h);
+        groups[t] = (W * H + 31) / 32;  // 32-pixel render items
+        for (int d = 0; d <= it.plan.max_depth; ++d) {
+            const bool in = d >= it.level_lo && d <= it.level_hi;
+            const int Ld = it.plan.level_off[d + 1] - it.plan.level_off[d];
+            const int nc = in ? Ld * it.cam->K * tiles_count[t] : 0;
+            const int nr = in ? it.plan.level_int[d] * groups[t] : 0;
+            const int id = lvl_base[t] + d;
+            segs[2 * (size_t)id] = SegInfo{t, d, 0, nc};
+            segs[2 * (size_t)id + 1] = SegInfo{t, d, 1, nr};
+            cnt_left[id] = nc;
+            rnd_left[id] = nr;
+            total += nc + nr;
+            n_nonempty += (nc > 0) + (nr > 0);
+        }
+    }
+    if (ctx->batch_debug_stall) {
+        // test hook: one level can never complete, so the waits behind it must run out
+        for (int t = 0; t < T; ++t)
+            if (items[t].level_hi > items[t].level_lo) {
+                cnt_left[lvl_base[t] + items[t].level_lo] += 1;
+                break;
+            }
+    }
+    // the count segment of each tree's first launched level is ready from the start
+    std::vector<int2> log0;
+    long long act_items = 0;
+    for (int t = 0; t < T; ++t) {
+        const int seg = 2 * (lvl_base[t] + items[t].level_lo);
+        if (items[t].level_lo > items[t].level_hi || segs[seg].items == 0) continue;
+        log0.push_back(make_int2((int)act_items, seg));
+        act_items += segs[seg].items;
+    }
+    if (total >= ((long long)1 << 31)) return fail(MIG_EINVAL, "tree_eval_batch: more than 2^31 work items in one batch");
+    const int log_cap = std::max(1, n_nonempty);
+    Carve cv;
+    const size_t o_segs = cv.take(sizeof(SegInfo) * std::max<size_t>(1, segs.size()));
+    const size_t o_cl = cv.take(4 * (size_t)total_levels), o_rl = cv.take(4 * (size_t)total_levels);
+    const size_t o_act = cv.take(8), o_work = cv.take(8);
+    const size_t o_log = cv.take(8 * (size_t)log_cap), o_valid = cv.take(4 * (size_t)log_cap);
+    struct TreeOff {
+        size_t node, ar, anc, loff, lint, lnodes, cnt, sel, out, arena;
+    };
+    std::vector<TreeOff> to(T);
+    for (int t = 0; t < T; ++t) {
+        const HostPlan &pl = items[t].plan;
+        const int n = pl.n, L = pl.max_depth + 1;
+        to[t].node = cv.take(16 * (size_t)n);
+        to[t].ar = cv.take(8 * (size_t)n);
+        to[t].anc = cv.take(4 * (size_t)std::max(1, pl.total_anc));
+        to[t].loff = cv.take(4 * (size_t)(L + 1));
+        to[t].lint = cv.take(4 * (size_t)L);
+        to[t].lnodes = cv.take(4 * (size_t)n);
+    }
+    const size_t up_bytes = cv.off;
+    const size_t zero_start = cv.off;
+    for (int t = 0; t < T; ++t) to[t].cnt = cv.take(8 * (size_t)items[t].plan.n * items[t].cam->K);
+    const size_t zero_bytes = cv.off - zero_start;
+    const size_t down_start = cv.off;
+    const size_t o_status = cv.take(64);
+    const bool tracing = ctx->batch_trace;
+    const size_t o_trace = cv.take(8 * (2 * segs.size() + 1));
+    for (int t = 0; t < T; ++t) to[t].out = cv.take(12 * (size_t)items[t].plan.n);
+    const size_t down_bytes = cv.off - down_start;
+    for (int t = 0; t < T; ++t) {
+        to[t].sel = cv.take(4 * (size_t)items[t].plan.n);
+        to[t].arena = cv.take(4 * (size_t)std::max(1, items[t].plan.n_internal) * items[t].cam->W * items[t].cam->H);
+    }
+    char *dev = nullptr;
+    mig_status st = ctx_workspace(ctx, cv.off, (void **)&dev);
+    if (st != MIG_OK) return st;
+    char *host = nullptr;
+    st = ctx_pinned(ctx, std::max(up_bytes, down_bytes) + 256, (void **)&host);
+    if (st != MIG_OK) return st;
+    MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    // ---- host image of the upload region
+    std::memset(host, 0, up_bytes);
+    std::unique_ptr<BatchParams> bpp(new BatchParams());
+    std::memset(bpp.get(), 0, sizeof(BatchParams));
+    BatchParams &bp = *bpp;
+    BatchTree *bt = bp.trees;
+    for (int t = 0; t < T; ++t) {
+        const BatchItem &it = items[t];
+        const HostPlan &pl = it.plan;
+        const int n = pl.n, L = pl.max_depth + 1;
+        std::memcpy(host + to[t].node, pl.node.data(), 16 * (size_t)n);
+        int2 *ar = (int2 *)(host + to[t].ar);
+        for (int i = 0; i < n; ++i) ar[i] = make_int2(pl.anc_off[i], pl.depth[i]);
+        if (pl.total_anc) std::memcpy(host + to[t].anc, pl.anc.data(), 4 * (size_t)pl.total_anc);
+        std::memcpy(host + to[t].loff, pl.level_off.data(), 4 * (size_t)(L + 1));
+        std::memcpy(host + to[t].lint, pl.level_int.data(), 4 * (size_t)L);
+        std::memcpy(host + to[t].lnodes, pl.level_nodes.data(), 4 * (size_t)n);
+        LevelParams p{};
+        mig_map *m = it.map;
+        p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
+        p.body = (const int4 *)it.cam->d_body;
+        p.yawtab = it.cam->d_yaw;
+        p.W = it.cam->W;
+        p.H = it.cam->H;
+        p.K = it.cam->K;
+        p.Tq = range_q16(it.sensor.range_m, m->voxel);
+        p.tile_w = tc.tile_w;
+        p.tile_h = tc.tile_h;
+        p.tiles_x = (p.W + tc.tile_w - 1) / tc.tile_w;
+        p.tiles = tiles_count[t];
+        p.level_off = (const int32_t *)(dev + to[t].loff);
+        p.level_int = (const int32_t *)(dev + to[t].lint);
+        p.level_nodes = (const int32_t *)(dev + to[t].lnodes);
+        p.node = (const int4 *)(dev + to[t].node);
+        p.anc_range = (const int2 *)(dev + to[t].ar);
+        p.anc = (const int32_t *)(dev + to[t].anc);
+        p.sel_yaw = (int32_t *)(dev + to[t].sel);
+        p.arena = (uint32_t *)(dev + to[t].arena);
+        p.cnt = (int32_t *)(dev + to[t].cnt);
+        p.work = nullptr;
+        p.out_abs = (int32_t *)(dev + to[t].out);
+        p.out_marg = p.out_abs + n;
+        p.out_yaw = p.out_abs + 2 * (size_t)n;
+        p.mode = it.mode;
+        p.lvl = 0;
+        p.stats = nullptr;
+        bt[t].p = p;
+        bt[t].lvl_base = lvl_base[t];
+        bt[t].n_levels = std::min(L, it.level_hi + 1);
+    }
+    if (!segs.empty()) std::memcpy(host + o_segs, segs.data(), sizeof(SegInfo) * segs.size());
+    std::memcpy(host + o_cl, cnt_left.data(), 4 * (size_t)total_levels);
+    std::memcpy(host + o_rl, rnd_left.data(), 4 * (size_t)total_levels);
+    *(unsigned long long *)(host + o_act) = ((unsigned long long)log0.size() << 40) | (unsigned long long)act_items;
+    *(long long *)(host + o_work) = 0;
+    if (!log0.empty()) std::memcpy(host + o_log, log0.data(), 8 * log0.size());
+    for (size_t e = 0; e < log0.size(); ++e) ((int *)(host + o_valid))[e] = 1;
+    bp.segs = (const SegInfo *)(dev + o_segs);
+    bp.n_levels_total = total_levels;
+    bp.total_items = total;
+    bp.act = (unsigned long long *)(dev + o_act);
+    bp.log = (int2 *)(dev + o_log);
+    bp.log_valid = (int *)(dev + o_valid);
+    bp.work = (long long *)(dev + o_work);
+    bp.count_left = (int *)(dev + o_cl);
+    bp.render_left = (int *)(dev + o_rl);
+    bp.status = (int *)(dev + o_status);
+    bp.trace = tracing ? (unsigned long long *)(dev + o_trace) : nullptr;
+    bp.n_segs_total = (int)segs.size();
+    bp.timeout_ns = (unsigned long long)ctx->batch_timeout_ns;
+    if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
+    mig_ctx::Batch *B = ctx->batch;
+    if (!B->ctas) B->ctas = batch_ctas_per_sm();
+    const int grid = ctx->num_sms * B->ctas;
+    // ---- graph: upload, zero counts and status, persistent kernel, download. The captured
+    // graph bakes in the kernel parameters and the copy sizes: replay only while all match.
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.bp = bp;
+    key.host = host;
+    key.up = up_bytes;
+    key.zero_start = zero_start;
+    key.zero = zero_bytes;
+    key.down_start = down_start;
+    key.down = down_bytes;
+    key.status = o_status;
+    key.grid = grid;
+    cudaStream_t s = ctx->stream;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dev, host, up_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && zero_bytes) e = cudaMemsetAsync(dev + zero_start, 0, zero_bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_status, 0, 64, s);
+        if (e != cudaSuccess) return e;
+        timed_launch(ctx, kProfBatch, [&] { launch_batch(bp, grid, s); });
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev + down_start, down_bytes, cudaMemcpyDeviceToHost, s);
+        return e;
+    };
+    const bool same = B->exec && std::memcmp(&B->key, &key, sizeof(key)) == 0 && !ctx->prof.on && !tracing;
+    if (same) {
+        // the kernel's parameters (bp) are baked into the graph; they depend only on the key
+        MIG_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+        B->replays++;
+    } else if (!ctx->prof.on && !tracing && s != nullptr) {
+        if (B->exec) {
+            cudaGraphExecDestroy(B->exec);
+            cudaGraphDestroy(B->graph);
+            B->exec = nullptr;
+            B->graph = nullptr;
+        }
+        MIG_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue();
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(MIG_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        MIG_CUDA_TRY(cudaGraphInstantiate(&B->exec, g, 0));
+        B->graph = g;
+        std::memcpy(&B->key, &key, sizeof(key));
+        B->captures++;
+        MIG_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+    } else {
+        // profiling or the legacy default stream (which cannot be captured): plain launches
+        cudaError_t e = enqueue();
+        if (e != cudaSuccess) return fail(MIG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    }
+    if (tracing) {
+        std::vector<unsigned long long> tr(2 * segs.size() + 1);
+        MIG_CUDA_TRY(cudaMemcpyAsync(tr.data(), dev + o_trace, 8 * tr.size(), cudaMemcpyDeviceToHost, s));
+        MIG_CUDA_TRY(cudaStreamSynchronize(s));
+        const unsigned long long t0 = tr[2 * segs.size()];
+        B->trace.clear();
+        for (size_t i = 0; i < segs.size(); ++i) {
+            if (!segs[i].items) continue;
+            mig_trace_rec rec{};
+            rec.tree = segs[i].tree;
+            rec.level = segs[i].level;
+            rec.phase = segs[i].render;
+            rec.items = segs[i].items;
+            rec.activated_us = tr[2 * i] ? (double)(long long)(tr[2 * i] - t0) * 1e-3 : 0.0;
+            rec.done_us = tr[2 * i + 1] ? (double)(long long)(tr[2 * i + 1] - t0) * 1e-3 : -1.0;
+            B->trace.push_back(rec);
+        }
+    }
+    MIG_CUDA_TRY(cudaStreamSynchronize(s));
+    const int *status = (const int *)host;
+    if (status[1]) return fail(MIG_ETIMEOUT, "batch: a device-side dependency wait ran out (no output is valid)");
+    if (status[0]) return fail(MIG_ECUDA, "batch: aborted");
+    for (int t = 0; t < T; ++t) {
+        const int n = items[t].plan.n;
+        const int32_t *o = (const int32_t *)(host + (to[t].out - down_start));
+        if (items[t].out_abs) std::memcpy(items[t].out_abs, o, 4 * (size_t)n);
+        if (items[t].out_marg) std::memcpy(items[t].out_marg, o + n, 4 * (size_t)n);
+        if (items[t].out_yaw) std::memcpy(items[t].out_yaw, o + 2 * (size_t)n, 4 * (size_t)n);
+    }
+    return MIG_OK;
+}
+
+// Alternative engine: each tree's chain of per-level kernels (count, select, render per level,
+// Sec. IV-C) on its own stream of a pool, forked from and joined back into the context stream,
+// captured into one CUDA graph. Kernels of different trees run concurrently and fill each
+// other's level tails and launch gaps, while every kernel keeps its parameters in the constant
+// bank (the per-level kernels' code).
+mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
+    const int T = (int)items.size();
+    const mig_tile_config tc = ctx->tiles;
+    Carve cv;
+    struct TreeOff {
+        size_t node, ar, anc, loff, lint, lnodes, cnt, work, sel, out, arena;
+    };
+    std::vector<TreeOff> to(T);
+    for (int t = 0; t < T; ++t) {
+        const HostPlan &pl = items[t].plan;
+        const int n = pl.n, L = pl.max_depth + 1;
+        to[t].node = cv.take(16 * (size_t)n);
+        to[t].ar = cv.take(8 * (size_t)n);
+        to[t].anc = cv.take(4 * (size_t)std::max(1, pl.total_anc));
+        to[t].loff = cv.take(4 * (size_t)(L + 1));
+        to[t].lint = cv.take(4 * (size_t)L);
+        to[t].lnodes = cv.take(4 * (size_t)n);
+    }
+    const size_t up_bytes = cv.off, zero_start = cv.off;
+    for (int t = 0; t < T; ++t) {
+        to[t].cnt = cv.take(8 * (size_t)items[t].plan.n * items[t].cam->K);
+        to[t].work = cv.take(4 * (size_t)(items[t].plan.max_depth + 1));
+    }
+    const size_t zero_bytes = cv.off - zero_start, down_start = cv.off;
+    for (int t = 0; t < T; ++t) to[t].out = cv.take(12 * (size_t)items[t].plan.n);
+    const size_t down_bytes = cv.off - down_start;
+    for (int t = 0; t < T; ++t) {
+        to[t].sel = cv.take(4 * (size_t)items[t].plan.n);
+        to[t].arena = cv.take(4 * (size_t)std::max(1, items[t].plan.n_internal) * items[t].cam->W * items[t].cam->H);
+    }
+    char *dev = nullptr;
+    mig_status st = ctx_workspace(ctx, cv.off, (void **)&dev);
+    if (st != MIG_OK) return st;
+    char *host = nullptr;
+    st = ctx_pinned(ctx, std::max(up_bytes, down_bytes) + 256, (void **)&host);
+    if (st != MIG_OK) return st;
+    MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    std::memset(host, 0, up_bytes);
+    std::vector<LevelParams> lp(T);
+    for (int t = 0; t < T; ++t) {
+        const BatchItem &it = items[t];
+        const HostPlan &pl = it.plan;
+        const int n = pl.n, L = pl.max_depth + 1;
+        std::memcpy(host + to[t].node, pl.node.data(), 16 * (size_t)n);
+        int2 *ar = (int2 *)(host + to[t].ar);
+        for (int i = 0; i < n; ++i) ar[i] = make_int2(pl.anc_off[i], pl.depth[i]);
+        if (pl.total_anc) std::memcpy(host + to[t].anc, pl.anc.data(), 4 * (size_t)pl.total_anc);
+        std::memcpy(host + to[t].loff, pl.level_off.data(), 4 * (size_t)(L + 1));
+        std::memcpy(host + to[t].lint, pl.level_int.data(), 4 * (size_t)L);
+        std::memcpy(host + to[t].lnodes, pl.level_nodes.data(), 4 * (size_t)n);
+        LevelParams p{};
+        mig_map *m = it.map;
+        p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
+        p.body = (const int4 *)it.cam->d_body;
+        p.yawtab = it.cam->d_yaw;
+        p.W = it.cam->W;
+        p.H = it.cam->H;
+        p.K = it.cam->K;
+        p.Tq = range_q16(it.sensor.range_m, m->voxel);
+        p.tile_w = tc.tile_w;
+        p.tile_h = tc.tile_h;
+        p.tiles_x = (p.W + tc.tile_w - 1) / tc.tile_w;
+        p.tiles = p.tiles_x * ((p.H + tc.tile_h - 1) / tc.tile_h);
+        p.level_off = (const int32_t *)(dev + to[t].loff);
+        p.level_int = (const int32_t *)(dev + to[t].lint);
+        p.level_nodes = (const int32_t *)(dev + to[t].lnodes);
+        p.node = (const int4 *)(dev + to[t].node);
+        p.anc_range = (const int2 *)(dev + to[t].ar);
+        p.anc = (const int32_t *)(dev + to[t].anc);
+        p.sel_yaw = (int32_t *)(dev + to[t].sel);
+        p.arena = (uint32_t *)(dev + to[t].arena);
+        p.cnt = (int32_t *)(dev + to[t].cnt);
+        p.work = (int32_t *)(dev + to[t].work);
+        p.out_abs = (int32_t *)(dev + to[t].out);
+        p.out_marg = p.out_abs + n;
+        p.out_yaw = p.out_abs + 2 * (size_t)n;
+        p.mode = it.mode;
+        lp[t] = p;
+    }
+    if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
+    mig_ctx::Batch *B = ctx->batch;
+    const int S = std::min(T, (int)B->kPool);
+    for (int i = (int)B->pool.size(); i < S; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        MIG_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        MIG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        B->pool.push_back(s);
+        B->join.push_back(e);
+    }
+    if (!B->fork) MIG_CUDA_TRY(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+    // longest trees first, round-robin over the pool
+    std::vector<int> order(T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return items[a].plan.n > items[c].plan.n; });
+    cudaStream_t s0 = ctx->stream;
+    const int cap = ctx->num_sms * 16, count_cap = ctx->num_sms * ctx->count_ctas;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dev, host, up_bytes, cudaMemcpyHostToDevice, s0);
+        if (e == cudaSuccess && zero_bytes) e = cudaMemsetAsync(dev + zero_start, 0, zero_bytes, s0);
+        if (e == cudaSuccess) e = cudaEventRecord(B->fork, s0);
+        for (int i = 0; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(B->pool[i], B->fork, 0);
+        for (int oi = 0; oi < T && e == cudaSuccess; ++oi) {
+            const int t = order[oi];
+            cudaStream_t s = B->pool[oi % S];
+            LevelParams p = lp[t];
+            const HostPlan &pl = items[t].plan;
+            const int rt = render_tiles(p.W, p.H);
+            for (int d = 0; d <= pl.max_depth; ++d) {
+                p.lvl = d;
+                const int Ld = pl.level_off[d + 1] - pl.level_off[d];
+                const int chunks = Ld * p.K * p.tiles;
+                launch_count(p, std::max(1, std::min((chunks + 7) / 8, count_cap)), s);
+                launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), s);
+                if (pl.level_int[d] > 0) launch_render(p, std::min(pl.level_int[d] * rt, cap), s);
+            }
+            e = cudaGetLastError();
+        }
+        for (int i = 0; i < S && e == cudaSuccess; ++i) e = cudaEventRecord(B->join[i], B->pool[i]);
+        for (int i = 0; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s0, B->join[i], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev + down_start, down_bytes, cudaMemcpyDeviceToHost, s0);
+        return e;
+    };
+    // graph key: every kernel parameter and copy is fixed by the trees' parameters and sizes
+    std::vector<char> key(sizeof(LevelParams) * T + 64 + 8 * T);
+    std::memcpy(key.data(), lp.data(), sizeof(LevelParams) * T);
+    size_t extra[8] = {(size_t)host, up_bytes, zero_bytes, down_bytes, (size_t)S, (size_t)count_cap, 0, 0};
+    std::memcpy(key.data() + sizeof(LevelParams) * T, extra, sizeof(extra));
+    for (int t = 0; t < T; ++t) {
+        const long long md = items[t].plan.max_depth;
+        std::memcpy(key.data() + sizeof(LevelParams) * T + 64 + 8 * t, &md, 8);
+    }
+    const bool same = B->sexec && B->skey == key && !ctx->prof.on;
+    if (same) {
+        MIG_CUDA_TRY(cudaGraphLaunch(B->sexec, s0));
+        B->replays++;
+    } else if (!ctx->prof.on && s0 != nullptr) {
+        if (B->sexec) {
+            cudaGraphExecDestroy(B->sexec);
+            cudaGraphDestroy(B->sgraph);
+            B->sexec = nullptr;
+            B->sgraph = nullptr;
+        }
+        MIG_CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue();
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s0, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(MIG_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        MIG_CUDA_TRY(cudaGraphInstantiate(&B->sexec, g, 0));
+        B->sgraph = g;
+        B->skey = key;
+        B->captures++;
+        MIG_CUDA_TRY(cudaGraphLaunch(B->sexec, s0));
+    } else {
+        cudaError_t e = enqueue();
+        if (e != cudaSuccess) return fail(MIG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    }
+    MIG_CUDA_TRY(cudaStreamSynchronize(s0));
+    for (int t = 0; t < T; ++t) {
+        const int n = items[t].plan.n;
+        const int32_t *o = (const int32_t *)(host + (to[t].out - down_start));
+        if (items[t].out_abs) std::memcpy(items[t].out_abs, o, 4 * (size_t)n);
+        if (items[t].out_marg) std::memcpy(items[t].out_marg, o + n, 4 * (size_t)n);
+        if (items[t].out_yaw) std::memcpy(items[t].out_yaw, o + 2 * (size_t)n, 4 * (size_t)n);
+    }
+    return MIG_OK;
+}
+
+}  // namespace
 
 extern "C" void mig_batch_release(mig_ctx *ctx) {
+    if (!ctx || !ctx->batch) return;
+    if (ctx->batch->exec) cudaGraphExecDestroy(ctx->batch->exec);
+    if (ctx->batch->graph) cudaGraphDestroy(ctx->batch->graph);
+    if (ctx->batch->sexec) cudaGraphExecDestroy(ctx->batch->sexec);
+    if (ctx->batch->sgraph) cudaGraphDestroy(ctx->batch->sgraph);
+    for (auto s : ctx->batch->pool) cudaStreamDestroy(s);
+    for (auto e : ctx->batch->join) cudaEventDestroy(e);
+    if (ctx->batch->fork) cudaEventDestroy(ctx->batch->fork);
     delete ctx->batch;
     ctx->batch = nullptr;
 }
 
 extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_tree_desc *trees) {
-    if (!ctx || (n_trees > 0 && !trees)) return mig::fail(MIG_EINVAL, "tree_eval_batch: NULL argument");
+    if (!ctx || n_trees < 0 || (n_trees > 0 && !trees)) return fail(MIG_EINVAL, "tree_eval_batch: invalid argument");
+    std::vector<BatchItem> items;
+    items.reserve(n_trees);
     for (int t = 0; t < n_trees; ++t) {
-        mig_eval_opts o{};
-        o.mode = trees[t].mode;
-        mig_status st = mig_tree_eval_ex(trees[t].map, trees[t].n_nodes, trees[t].parent, trees[t].pos_m,
-                                         &trees[t].sensor, &o, trees[t].abs_gain, trees[t].marg_gain, trees[t].best_yaw);
+        const mig_tree_desc &d = trees[t];
+        if (!d.map || d.map->ctx != ctx) return fail(MIG_EINVAL, "tree_eval_batch: tree " + std::to_string(t) + " has no map of this context");
+        if (d.mode < 0 || d.mode > 2) return fail(MIG_EINVAL, "tree_eval_batch: unknown mode");
+        if (d.n_nodes < 0) return fail(MIG_EINVAL, "tree_eval_batch: negative node count");
+        if (d.n_nodes > 0 && (!d.abs_gain || !d.marg_gain || !d.best_yaw))
+            return fail(MIG_EINVAL, "tree_eval_batch: output array is NULL");
+        mig_status st = sensor_check(d.sensor, d.map->voxel);
+        if (st != MIG_OK) return st;
+        if (d.n_nodes == 0) continue;
+        BatchItem it;
+        it.map = d.map;
+        it.n = d.n_nodes;
+        it.parent = d.parent;
+        it.pos = d.pos_m;
+        it.sensor = d.sensor;
+        it.mode = d.mode;
+        it.out_abs = d.abs_gain;
+        it.out_marg = d.marg_gain;
+        it.out_yaw = d.best_yaw;
+        const int dims[3] = {d.map->nx, d.map->ny, d.map->nz};
+        st = plan_build(d.n_nodes, d.parent, d.pos_m, d.map->origin, d.map->voxel, dims, it.plan);
+        if (st != MIG_OK) return st;
+        it.level_lo = 0;
+        it.level_hi = it.plan.max_depth;
+        items.push_back(std::move(it));
+    }
+    if (items.empty()) return MIG_OK;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    MIG_CUDA_TRY(cudaSetDevice(ctx->device));
+    for (auto &it : items) {
+        mig_status st = ctx_camera(ctx, it.sensor, &it.cam);
+        if (st != MIG_OK) return st;
+    }
+    if (ctx->tiles.engine == 1) return batch_run_streams(ctx, items);
+    if ((int)items.size() <= kBatchMaxTrees) return batch_run(ctx, items);
+    for (size_t s = 0; s < items.size(); s += kBatchMaxTrees) {  // one persistent launch per group
+        std::vector<BatchItem> part(std::make_move_iterator(items.begin() + s),
+                                    std::make_move_iterator(items.begin() + std::min(items.size(), s + kBatchMaxTrees)));
+        mig_status st = batch_run(ctx, part);
         if (st != MIG_OK) return st;
     }
     return MIG_OK;
 }
 
 extern "C" mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg) {
-    if (!ctx || !cfg) return mig::fail(MIG_EINVAL, "batch_set_tiles: NULL argument");
+    if (!ctx || !cfg) return fail(MIG_EINVAL, "batch_set_tiles: NULL argument");
     if (cfg->tile_w < 1 || cfg->tile_h < 1 || cfg->tile_w * cfg->tile_h > 4096 || (cfg->tile_w * cfg->tile_h) % 32 != 0 ||
-        cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 32)
-        return mig::fail(MIG_EINVAL, "batch_set_tiles: a tile holds a multiple of 32 rays, at most 4096");
+        cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 32 || cfg->engine < 0 || cfg->engine > 1)
+        return fail(MIG_EINVAL, "batch_set_tiles: a tile holds a multiple of 32 rays, at most 4096; engine 0 or 1");
+    std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->tiles = *cfg;
     return MIG_OK;
 }
 
 extern "C" mig_status mig_batch_get_tiles(mig_ctx *ctx, mig_tile_config *cfg) {
-    if (!ctx || !cfg) return mig::fail(MIG_EINVAL, "batch_get_tiles: NULL argument");
+    if (!ctx || !cfg) return fail(MIG_EINVAL, "batch_get_tiles: NULL argument");
     *cfg = ctx->tiles;
+    return MIG_OK;
+}
+
+extern "C" mig_status mig_batch_set_timeout(mig_ctx *ctx, int64_t timeout_us, int debug_stall) {
+    if (!ctx || timeout_us < 1) return fail(MIG_EINVAL, "batch_set_timeout: invalid argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->batch_timeout_ns = timeout_us * 1000;
+    ctx->batch_debug_stall = debug_stall != 0;
+    return MIG_OK;
+}
+
+extern "C" mig_status mig_batch_graph_stats(mig_ctx *ctx, uint64_t *captures, uint64_t *replays) {
+    if (!ctx) return fail(MIG_EINVAL, "batch_graph_stats: NULL argument");
+    if (captures) *captures = ctx->batch ? ctx->batch->captures : 0;
+    if (replays) *replays = ctx->batch ? ctx->batch->replays : 0;
+    return MIG_OK;
+}
+
+extern "C" mig_status mig_batch_trace(mig_ctx *ctx, int enable) {
+    if (!ctx) return fail(MIG_EINVAL, "batch_trace: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->batch_trace = enable != 0;
+    return MIG_OK;
+}
+
+extern "C" mig_status mig_batch_trace_read(mig_ctx *ctx, mig_trace_rec *out, int cap, int *n) {
+    if (!ctx || !n || (cap > 0 && !out)) return fail(MIG_EINVAL, "batch_trace_read: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const int m = ctx->batch ? (int)ctx->batch->trace.size() : 0;
+    *n = m;
+    for (int i = 0; i < std::min(m, cap); ++i) out[i] = ctx->batch->trace[i];
     return MIG_OK;
 }

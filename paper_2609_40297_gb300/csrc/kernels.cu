@@ -8,404 +8,31 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "dev_path.cuh"
 #include "kernels.h"
 #include "mig.h"
-
-// Voxel layout of the device grid: 0 = 8x8x8 bricks of 512 B (z-major inside a brick),
-// 1 = x-fastest rows (the host order), stepped with an incremental address.
-#ifndef MIG_LAYOUT
-#define MIG_LAYOUT 1
-#endif
-// 1 = branch-free axis step (selects), 0 = three-way branch.
-#ifndef MIG_BRANCHLESS
-#define MIG_BRANCHLESS 1
-#endif
-// Minimum resident count-kernel CTAs per SM requested from the register allocator.
-#ifndef MIG_COUNT_MINB
-#define MIG_COUNT_MINB 4
-#endif
 
 namespace mig {
 
 namespace {
 
-constexpr int kOcc = 2;
-constexpr int kUnknown = 0;
-constexpr uint32_t kQ16 = 65536;
-
-__device__ __forceinline__ uint32_t voxel_addr(const GridView &G, int x, int y, int z) {
-#if MIG_LAYOUT == 1
-    return ((uint32_t)z * (uint32_t)G.ny + (uint32_t)y) * (uint32_t)G.nx + (uint32_t)x;
-#else
-    const uint32_t b = ((uint32_t)(z >> 3) * (uint32_t)G.nby + (uint32_t)(y >> 3)) * (uint32_t)G.nbx + (uint32_t)(x >> 3);
-    return (b << 9) | ((uint32_t)(z & 7) << 6) | ((uint32_t)(y & 7) << 3) | (uint32_t)(x & 7);
-#endif
-}
-
-// Per-axis DDA set-up (Sec. IV-B, Amanatides-Woo). n = distance to the next face (Q16),
-// ad = |d| (Q30); rem = number of face crossings along this axis that stay inside the grid
-// and start before the range T (crossing k is at t = (n + k 2^16) / ad, allowed iff < T).
-__device__ __forceinline__ void axis_init(int P, int d, int N, int64_t Tq, int &v, uint32_t &n, uint32_t &ad, int &s,
-                                          int &rem) {
-    v = P >> 16;
-    int grid_rem;
-    if (d > 0) {
-        s = 1;
-        ad = (uint32_t)d;
-        n = (uint32_t)(((v + 1) << 16) - P);
-        grid_rem = N - 1 - v;
-    } else if (d < 0) {
-        s = -1;
-        ad = (uint32_t)(-d);
-        n = (uint32_t)(P - (v << 16));
-        grid_rem = v;
-    } else {
-        s = 0;
-        ad = 0;
-        n = kQ16;
-        rem = 0;
-        return;
-    }
-    const uint64_t lim = ((uint64_t)Tq * ad + ((1ull << 30) - 1)) >> 30;  // n >= lim  <=>  t >= T
-    const int64_t range_rem = (n >= lim) ? 0 : (int64_t)((lim - n + (kQ16 - 1)) >> 16);
-    rem = (int)min((int64_t)grid_rem, range_rem);
-}
-
-struct RayIn {
-    int vx, vy, vz;
-    uint32_t nx, ny, nz, adx, ady, adz;
-    int sx, sy, sz, rx, ry, rz;
-#if MIG_LAYOUT == 1
-    uint32_t addr;
-    int dax, day, daz;  // signed address strides of one step along each axis
-#endif
-};
-
-__device__ __forceinline__ void ray_init(RayIn &r, const GridView &G, int Px, int Py, int Pz, int dx, int dy, int dz,
-                                         int64_t Tq) {
-    axis_init(Px, dx, G.nx, Tq, r.vx, r.nx, r.adx, r.sx, r.rx);
-    axis_init(Py, dy, G.ny, Tq, r.vy, r.ny, r.ady, r.sy, r.ry);
-    axis_init(Pz, dz, G.nz, Tq, r.vz, r.nz, r.adz, r.sz, r.rz);
-#if MIG_LAYOUT == 1
-    r.addr = voxel_addr(G, r.vx, r.vy, r.vz);
-    r.dax = r.sx;
-    r.day = r.sy * G.nx;
-    r.daz = r.sz * G.nx * G.ny;
-#endif
-}
-
-__device__ __forceinline__ uint32_t ray_addr(const RayIn &r, const GridView &G) {
-#if MIG_LAYOUT == 1
-    (void)G;
-    return r.addr;
-#else
-    return voxel_addr(G, r.vx, r.vy, r.vz);
-#endif
-}
-
-// World direction of (yaw k, pixel): yaw rotation of the body-frame ray, floored (Q30).
-__device__ __forceinline__ void ray_dir(const int4 b, int ck, int sk, int &dx, int &dy, int &dz) {
-    const int64_t bx = b.x, by = b.y;
-    dx = (int)(((int64_t)ck * bx - (int64_t)sk * by) >> 30);
-    dy = (int)(((int64_t)sk * bx + (int64_t)ck * by) >> 30);
-    dz = b.z;
-}
-
-// One step of the DDA: picks the axis with the smallest next crossing (ties x, y, z), stops if
-// that crossing leaves the grid or starts at t >= T. Returns false when the ray ends.
-// DEPTH: also report the entry face distance / speed (ne / ade) of the new voxel.
-template <bool DEPTH>
-__device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) {
-    const uint64_t xy = (uint64_t)r.nx * r.ady, yx = (uint64_t)r.ny * r.adx;
-    const uint64_t xz = (uint64_t)r.nx * r.adz, zx = (uint64_t)r.nz * r.adx;
-    const uint64_t yz = (uint64_t)r.ny * r.adz, zy = (uint64_t)r.nz * r.ady;
-#if MIG_BRANCHLESS
-    const bool bx = (xy <= yx) && (xz <= zx);
-    const bool by = !bx && (yz <= zy);
-    const bool bz = !bx && !by;
-    const int rem = bx ? r.rx : (by ? r.ry : r.rz);
-    if (rem == 0) return false;
-    if constexpr (DEPTH) {
-        ne = bx ? r.nx : (by ? r.ny : r.nz);
-        ade = bx ? r.adx : (by ? r.ady : r.adz);
-    }
-    r.rx -= bx;
-    r.ry -= by;
-    r.rz -= bz;
-    r.nx += bx ? kQ16 : 0u;
-    r.ny += by ? kQ16 : 0u;
-    r.nz += bz ? kQ16 : 0u;
-    r.vx += bx ? r.sx : 0;
-    r.vy += by ? r.sy : 0;
-    r.vz += bz ? r.sz : 0;
-#if MIG_LAYOUT == 1
-    r.addr += bx ? r.dax : (by ? r.day : r.daz);
-#endif
-    return true;
-#else
-    if (xy <= yx && xz <= zx) {
-        if (r.rx == 0) return false;
-        --r.rx;
-        ne = r.nx;
-        ade = r.adx;
-        r.nx += kQ16;
-        r.vx += r.sx;
-#if MIG_LAYOUT == 1
-        r.addr += r.dax;
-#endif
-    } else if (yz <= zy) {
-        if (r.ry == 0) return false;
-        --r.ry;
-        ne = r.ny;
-        ade = r.ady;
-        r.ny += kQ16;
-        r.vy += r.sy;
-#if MIG_LAYOUT == 1
-        r.addr += r.day;
-#endif
-    } else {
-        if (r.rz == 0) return false;
-        --r.rz;
-        ne = r.nz;
-        ade = r.adz;
-        r.nz += kQ16;
-        r.vz += r.sz;
-#if MIG_LAYOUT == 1
-        r.addr += r.daz;
-#endif
-    }
-    return true;
-#endif
-}
-
-// Depth (Q16.16 voxel units, camera z) of the entry point t_e = ne / ade of the hit voxel, or
-// of the range endpoint.
-__device__ __forceinline__ uint32_t hit_depth(bool hit, uint32_t ne, uint32_t ade, int dzc, int64_t Tq) {
-    if (hit) return (uint32_t)(((uint64_t)ne * (uint32_t)dzc) / ade);
-    return (uint32_t)(((uint64_t)Tq * (uint32_t)dzc) >> 30);
-}
-
-__device__ __forceinline__ void decode_item(const LevelParams &p, int item, int &li, int &k, int &tile) {
-    tile = item % p.tiles;
-    const int rest = item / p.tiles;
-    k = rest % p.K;
-    li = rest / p.K;
-}
-
-// ------------------------------------------------------------------------------- count kernel
-// Work item = (node of the level, yaw k, tile of tile_w x tile_h pixel rays), taken by one warp
-// from the level's atomic work counter (no CTA barrier: warps never wait for each other). Lane l
-// casts rays l, l+32, ... of the tile and starts its next ray as soon as the current one ends.
-// Unknown voxels owned by the ray (A1: the voxel centre projects into this pixel) count as
-// absolute gain; their coordinates go to a per-warp queue, and each full batch of 32 samples is
-// tested against the ancestors' depth buffers with all 32 lanes at once (Sec. IV-B), so the
-// rare, long ancestor test never runs one lane at a time.
-constexpr int kWarps = 8;
-
-struct AncRec {
-    int px, py, pz, yaw;
-    float fx, fy, fz;  // P / 2^16 - 1/2 (voxel units): voxel centre offset for the float estimate
-    float m[9];        // projection rows / 2^16 (float estimate of U, V, Z)
-    const uint32_t *D;
-};
-
-__device__ __forceinline__ float small_int_to_float(int v) {  // exact for 0 <= v < 2^23
-    return __int_as_float(0x4B000000 | v) - 8388608.0f;
-}
-
-// floor(U / Z) for 0 <= U < bound * Z, Z > 0, from a float estimate, corrected exactly.
-__device__ __forceinline__ int floor_div_from(int64_t U, int64_t Z, float est, int bound) {
-    int q = __float_as_int(est - 0.5f + 12582912.0f) - 0x4B400000;  // nearest of est - 1/2
-    q = max(0, min(q, bound - 1));
-    while (q > 0 && (int64_t)q * Z > U) --q;
-    while (q < bound - 1 && (int64_t)(q + 1) * Z <= U) ++q;
-    return q;
-}
-
-// Sec. IV-B: is the centre of voxel (x, y, z) observed by any ancestor (z <= stored depth)?
-template <bool STATS>
-__device__ __forceinline__ bool observed(const LevelParams &p, const AncRec *anc, int na, int x, int y, int z,
-                                         uint32_t &st_anc, uint32_t &st_reads) {
-    const float xf = small_int_to_float(x), yf = small_int_to_float(y), zf = small_int_to_float(z);
-    for (int a = 0; a < na; ++a) {
-        const AncRec &A = anc[a];
-        const int ax = (x << 16) + 32768 - A.px;
-        const int ay = (y << 16) + 32768 - A.py;
-        const int az = (z << 16) + 32768 - A.pz;
-        const int4 *row = reinterpret_cast<const int4 *>(p.yawtab + A.yaw * 12);
-        const int4 r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2);  // ck sk mu0 mu1 | mu2 mv0 mv1 mv2 | mz0 mz1 mz2 -
-        const int64_t Za = (int64_t)r2.x * ax + (int64_t)r2.y * ay + (int64_t)r2.z * az;
-        if constexpr (STATS) ++st_anc;
-        if (Za <= 0) continue;
-        const int64_t Ua = (int64_t)r0.z * ax + (int64_t)r0.w * ay + (int64_t)r1.x * az;
-        if (Ua < 0 || Ua >= (int64_t)p.W * Za) continue;
-        const int64_t Va = (int64_t)r1.y * ax + (int64_t)r1.z * ay + (int64_t)r1.w * az;
-        if (Va < 0 || Va >= (int64_t)p.H * Za) continue;
-        const float rx = xf - A.fx, ry = yf - A.fy, rz = zf - A.fz;
-        const float zi = __frcp_rn(fmaf(A.m[6], rx, fmaf(A.m[7], ry, A.m[8] * rz)));
-        const float uf = fmaf(A.m[0], rx, fmaf(A.m[1], ry, A.m[2] * rz)) * zi;
-        const float vf = fmaf(A.m[3], rx, fmaf(A.m[4], ry, A.m[5] * rz)) * zi;
-        const int pu = floor_div_from(Ua, Za, uf, p.W);
-        const int pv = floor_div_from(Va, Za, vf, p.H);
-        const uint32_t D = __ldg(A.D + pv * p.W + pu);
-        if constexpr (STATS) ++st_reads;
-        if (Za < (((int64_t)D + 1) << 16)) return true;  // z <= D
-    }
-    return false;
-}
+using namespace dev;
 
 template <bool STATS>
 __global__ void __launch_bounds__(kWarps * 32, MIG_COUNT_MINB) count_kernel(const LevelParams p) {
     __shared__ AncRec s_anc[kWarps][MIG_MAX_DEPTH];
     __shared__ unsigned long long s_q[kWarps][64];
+    __shared__ int4 s_cam[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    AncRec *anc = s_anc[warp];
-    unsigned long long *q = s_q[warp];
     const int l0 = p.level_off[p.lvl];
     const int L = p.level_off[p.lvl + 1] - l0;
     const int chunks = L * p.K * p.tiles;
-    const unsigned lt_mask = (1u << lane) - 1u;
     for (;;) {
         int c = 0;
         if (lane == 0) c = atomicAdd(p.work + p.lvl, 1);
         c = __shfl_sync(0xffffffffu, c, 0);
         if (c >= chunks) break;
-        int li, k, tile;
-        decode_item(p, c, li, k, tile);
-        const int n = p.level_nodes[l0 + li];
-        const int4 nd = p.node[n];
-        const int2 ar = p.anc_range[n];
-        int na = ar.y;
-        if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
-        else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
-        __syncwarp();
-        for (int t = lane; t < na; t += 32) {
-            const int a = p.anc[ar.x + t];
-            const int4 an = p.node[a];
-            const int y = p.sel_yaw[a];
-            const int32_t *yr = p.yawtab + y * 12;
-            AncRec r;
-            r.px = an.x;
-            r.py = an.y;
-            r.pz = an.z;
-            r.yaw = y;
-            r.fx = (float)an.x * (1.0f / 65536.0f) - 0.5f;
-            r.fy = (float)an.y * (1.0f / 65536.0f) - 0.5f;
-            r.fz = (float)an.z * (1.0f / 65536.0f) - 0.5f;
-#pragma unroll
-            for (int qq = 0; qq < 9; ++qq) r.m[qq] = (float)yr[2 + qq] * (1.0f / 65536.0f);
-            r.D = p.arena + (size_t)an.w * p.W * p.H;
-            anc[t] = r;
-        }
-        __syncwarp();
-        const int32_t *yk = p.yawtab + k * 12;
-        const int ck = yk[0], sk = yk[1];
-        const int mu0 = yk[2], mu1 = yk[3], mu2 = yk[4];
-        const int mv0 = yk[5], mv1 = yk[6], mv2 = yk[7];
-        const int mz0 = yk[8], mz1 = yk[9], mz2 = yk[10];
-        const int tx0 = (tile % p.tiles_x) * p.tile_w, ty0 = (tile / p.tiles_x) * p.tile_h;
-        const int tile_rays = p.tile_w * p.tile_h;
-        int next = 0, ti = 0, tj = 0, qn = 0, c_abs = 0, c_mrg = 0;
-        bool have = false;
-        RayIn r;
-        uint32_t ne = 0, ade = 1;
-        uint32_t st_steps = 0, st_unk = 0, st_anc = 0, st_reads = 0, st_rays = 0;
-        for (;;) {
-            // lanes without a ray take the chunk's next rays in order (neighbouring pixels)
-            const unsigned need = __ballot_sync(0xffffffffu, !have);
-            if (need && next < tile_rays) {
-                const int idx = next + __popc(need & lt_mask);
-                next += __popc(need);
-                if (!have && idx < tile_rays) {
-                    ti = tx0 + idx % p.tile_w;
-                    tj = ty0 + idx / p.tile_w;
-                    if (ti < p.W && tj < p.H) {
-                        const int4 b = p.body[tj * p.W + ti];
-                        int dx, dy, dz;
-                        ray_dir(b, ck, sk, dx, dy, dz);
-                        ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
-                        have = true;
-                        if constexpr (STATS) ++st_rays;
-                    }
-                }
-            }
-            if (!__any_sync(0xffffffffu, have)) {
-                if (next >= tile_rays) break;
-                continue;
-            }
-            bool owned = false;
-            unsigned long long samp = 0;
-            if (have) {
-                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
-                if constexpr (STATS) ++st_steps;
-                if (code == kOcc) {
-                    have = false;
-                } else {
-                    if (code == kUnknown) {
-                        if constexpr (STATS) ++st_unk;
-                        // owner test: centre of this voxel projects into pixel (ti, tj)
-                        const int rx = (r.vx << 16) + 32768 - nd.x;
-                        const int ry = (r.vy << 16) + 32768 - nd.y;
-                        const int rz = (r.vz << 16) + 32768 - nd.z;
-                        const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * rz;
-                        const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * rz;
-                        const int64_t iZ = (int64_t)ti * Z;
-                        if (Z > 0 && U >= iZ && U < iZ + Z) {
-                            const int64_t V = (int64_t)mv0 * rx + (int64_t)mv1 * ry + (int64_t)mv2 * rz;
-                            const int64_t jZ = (int64_t)tj * Z;
-                            owned = V >= jZ && V < jZ + Z;
-                            samp = (unsigned long long)(uint32_t)r.vx | ((unsigned long long)(uint32_t)r.vy << 16) |
-                                   ((unsigned long long)(uint32_t)r.vz << 32);
-                        }
-                    }
-                    have = ray_step<false>(r, ne, ade);
-                }
-            }
-            c_abs += owned;
-            const unsigned bal = __ballot_sync(0xffffffffu, owned);
-            if (bal) {
-                if (owned) q[qn + __popc(bal & lt_mask)] = samp;
-                qn += __popc(bal);
-                if (qn >= 32) {  // a full batch: every lane tests one sample (Sec. IV-B)
-                    __syncwarp();
-                    const unsigned long long s = q[lane];
-                    const int sx = (int)(s & 0xFFFF), sy = (int)((s >> 16) & 0xFFFF), sz = (int)(s >> 32);
-                    c_mrg += !observed<STATS>(p, anc, na, sx, sy, sz, st_anc, st_reads);
-                    __syncwarp();
-                    if (lane < qn - 32) q[lane] = q[lane + 32];
-                    __syncwarp();
-                    qn -= 32;
-                }
-            }
-        }
-        // the last, partial batch
-        __syncwarp();
-        if (lane < qn) {
-            const unsigned long long s = q[lane];
-            const int sx = (int)(s & 0xFFFF), sy = (int)((s >> 16) & 0xFFFF), sz = (int)(s >> 32);
-            c_mrg += !observed<STATS>(p, anc, na, sx, sy, sz, st_anc, st_reads);
-        }
-        c_abs = __reduce_add_sync(0xffffffffu, c_abs);
-        c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);
-        if (lane == 0 && (c_abs | c_mrg)) {
-            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2, c_abs);
-            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2 + 1, c_mrg);
-        }
-        if constexpr (STATS) {
-            st_rays = __reduce_add_sync(0xffffffffu, st_rays);
-            st_steps = __reduce_add_sync(0xffffffffu, st_steps);
-            st_unk = __reduce_add_sync(0xffffffffu, st_unk);
-            st_anc = __reduce_add_sync(0xffffffffu, st_anc);
-            st_reads = __reduce_add_sync(0xffffffffu, st_reads);
-            if (lane == 0) {
-                atomicAdd(p.stats + 0, (unsigned long long)st_rays);
-                atomicAdd(p.stats + 1, (unsigned long long)st_steps);
-                atomicAdd(p.stats + 2, (unsigned long long)st_unk);
-                atomicAdd(p.stats + 3, (unsigned long long)(uint32_t)c_abs);
-                atomicAdd(p.stats + 4, (unsigned long long)st_anc);
-                atomicAdd(p.stats + 5, (unsigned long long)st_reads);
-            }
-        }
+        count_chunk<STATS>(p, HotDirect{p}, l0, c, s_anc[warp], s_q[warp], s_cam[warp], lane);
     }
 }
 
@@ -415,23 +42,8 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_COUNT_MINB) count_kernel(cons
 __global__ void select_kernel(const LevelParams p) {
     const int l0 = p.level_off[p.lvl];
     const int L = p.level_off[p.lvl + 1] - l0;
-    for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < L; li += gridDim.x * blockDim.x) {
-        const int n = p.level_nodes[l0 + li];
-        const int32_t *c = p.cnt + (size_t)n * p.K * 2;
-        int best = 0, bm = c[1], amax = c[0];
-        for (int k = 1; k < p.K; ++k) {
-            const int m = c[2 * k + 1];
-            if (m > bm) {
-                bm = m;
-                best = k;
-            }
-            amax = max(amax, c[2 * k]);
-        }
-        p.sel_yaw[n] = best;
-        p.out_abs[n] = amax;
-        p.out_marg[n] = bm;
-        p.out_yaw[n] = best;
-    }
+    for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < L; li += gridDim.x * blockDim.x)
+        select_node(p, p.level_nodes[l0 + li]);
 }
 
 // ------------------------------------------------------------------------------ render kernel
@@ -456,25 +68,7 @@ __global__ void __launch_bounds__(256) render_kernel(const LevelParams p) {
         const int ti = (tile % rtx) * RT + tid % RT;
         const int tj = (tile / rtx) * RT + tid / RT;
         if (ti >= p.W || tj >= p.H) continue;
-        const int32_t *yk = p.yawtab + p.sel_yaw[n] * 12;
-        const int4 b = p.body[tj * p.W + ti];
-        int dx, dy, dz;
-        ray_dir(b, yk[0], yk[1], dx, dy, dz);
-        RayIn r;
-        ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
-        uint32_t ne = 0, ade = 1;
-        bool hit = false;
-        uint32_t st_steps = 0;
-        for (;;) {
-            const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
-            if constexpr (STATS) ++st_steps;
-            if (code == kOcc) {
-                hit = true;
-                break;
-            }
-            if (!ray_step<true>(r, ne, ade)) break;
-        }
-        p.arena[(size_t)nd.w * p.W * p.H + (size_t)tj * p.W + ti] = hit_depth(hit, ne, ade, b.w, p.Tq);
+        const uint32_t st_steps = render_pixel(p, n, nd, ti, tj);
         if constexpr (STATS) {
             atomicAdd(p.stats + 6, 1ull);
             atomicAdd(p.stats + 7, (unsigned long long)st_steps);

@@ -103,8 +103,11 @@ struct mig_ctx {
     void *pinned = nullptr;  // pinned host staging
     size_t pinned_bytes = 0;
     int32_t *d_err = nullptr;  // device-side check word (device planning)
-    mig_tile_config tiles{4, 16, 4};  // count-pass tile: 64 rays per warp work item
+    mig_tile_config tiles{4, 16, 4, 1};  // 64-ray count tiles; batches on stream chains
     mig::Profiler prof;
+    int64_t batch_timeout_ns = 5000000000LL;  // bound of every device-side wait of the batch kernel
+    bool batch_debug_stall = false;           // test hook: one level never completes
+    bool batch_trace = false;                 // record per-segment device timestamps
     struct Batch;            // batched engine state (batch.cu)
     Batch *batch = nullptr;
     std::mutex mu;           // serialises calls that share the workspace

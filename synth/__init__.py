@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import hashlib
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -145,15 +146,18 @@ def world_rooms(rng, nx=400, ny=400, nz=100, wall=2, slab=2, target=0.10):
                 occ[slab:slab + door_h, c:c + wall, s:s + w] = False
     # pillars (full height) and low furniture boxes until the target fraction
     total = occ.size
-    while occ.sum() < target * total:
+    count = int(occ.sum())
+    while count < target * total:
         if rng.random() < 0.5:
             px, py = (int(v) for v in rng.integers(0, [nx - 4, ny - 4]))
-            occ[:, py:py + 4, px:px + 4] = True
+            sl = occ[:, py:py + 4, px:px + 4]
         else:
             ex, ey, ez = (int(v) for v in rng.integers([6, 6, 4], [30, 30, 15]))
             px = int(rng.integers(0, nx - ex))
             py = int(rng.integers(0, ny - ey))
-            occ[slab:slab + ez, py:py + ey, px:px + ex] = True
+            sl = occ[slab:slab + ez, py:py + ey, px:px + ex]
+        count += int(sl.size - np.count_nonzero(sl))
+        sl[...] = True
     return occ
 
 
@@ -390,7 +394,7 @@ def tiny(seed=101, n_nodes=20, max_depth=4) -> Problem:
     return Problem("tiny", m, tree, SENSOR_TINY, {"seed": seed})
 
 
-def rooms_map(seed, nx=400, ny=400, nz=100, v=0.1, n_views=5, scan_range=6.0):
+def rooms_map(seed, nx=400, ny=400, nz=100, v=0.1, n_views=5, scan_range=6.0, scan_step_deg=0.5):
     rng = np.random.default_rng(seed)
     truth = world_rooms(rng, nx, ny, nz)
     org = (0.0, 0.0, 0.0)
@@ -400,7 +404,7 @@ def rooms_map(seed, nx=400, ny=400, nz=100, v=0.1, n_views=5, scan_range=6.0):
     c0 = np.floor((vp0 - np.asarray(org)) / v).astype(int)
     while len(vps) < n_views:
         vps.append(_free_spot(rng, truth, v, org, (c0[0] - 80, c0[1] - 80), (c0[0] + 80, c0[1] + 80), zv))
-    grid = explore(truth, v, org, vps, scan_range)
+    grid = explore(truth, v, org, vps, scan_range, az_step_deg=scan_step_deg, el_step_deg=scan_step_deg)
     return MapSpec(grid, v, org, truth=truth), vps, rng
 
 
@@ -444,19 +448,30 @@ def large(seed=303, n_nodes=2000, max_depth=15) -> Problem:
 RAY_GRIDS = [(64, 48), (96, 72), (128, 96), (160, 120), (240, 180), (320, 240)]
 
 
-def batched(seed_base=404, n_trees=64, n_range=(50, 2000), depth_range=(3, 15)):
-    """64 independent problems on 64 seeded rooms maps (config-2 type): tree sizes
-    U[50,2000], depth limits U[3,15], ray grids drawn from RAY_GRIDS, K=16, 6 m."""
-    out = []
-    for i in range(n_trees):
-        m, vps, rng = rooms_map(seed_base + i)
-        n = int(rng.integers(n_range[0], n_range[1] + 1))
-        dmax = int(rng.integers(depth_range[0], depth_range[1] + 1))
-        w, h = RAY_GRIDS[int(rng.integers(0, len(RAY_GRIDS)))]
-        tree = rrt(rng, m, vps[0], n, dmax, 1.5, max_children=6, box=local_box(m, vps[0], 8.0, 1.0, 1.5))
-        s = Sensor(90.0, 60.0, w, h, 6.0, 16, 0.0)
-        out.append(Problem(f"batched_{i}", m, tree, s, {"seed": seed_base + i}))
-    return out
+def _batched_one(args):
+    seed, n_range, depth_range = args
+    m, vps, rng = rooms_map(seed, scan_step_deg=1.0)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    dmax = int(rng.integers(depth_range[0], depth_range[1] + 1))
+    w, h = RAY_GRIDS[int(rng.integers(0, len(RAY_GRIDS)))]
+    tree = rrt(rng, m, vps[0], n, dmax, 1.5, max_children=6, box=local_box(m, vps[0], 8.0, 1.0, 1.5))
+    s = Sensor(90.0, 60.0, w, h, 6.0, 16, 0.0)
+    m.truth = None  # not needed downstream; keeps the pickled result small
+    return Problem(f"batched_{seed}", m, tree, s, {"seed": seed})
+
+
+def batched(seed_base=404, n_trees=64, n_range=(50, 2000), depth_range=(3, 15), workers=None):
+    """64 independent problems on 64 seeded rooms maps (config-2 type, scans at 1 deg): tree sizes
+    U[50,2000], depth limits U[3,15], ray grids drawn from RAY_GRIDS, K=16, 6 m. Built in a pool
+    of spawned worker processes when workers > 1."""
+    jobs = [(seed_base + i, n_range, depth_range) for i in range(n_trees)]
+    workers = workers if workers is not None else min(16, os.cpu_count() or 1)
+    if workers <= 1 or n_trees <= 1:
+        return [_batched_one(j) for j in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batched_one, jobs))
 
 
 def map_update_box(rng, m: MapSpec, frac=0.10):

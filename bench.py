@@ -390,6 +390,118 @@ def run_batched(args):
     return res
 
 
+# ----------------------------------------------------------------------------- serving (config 5)
+def run_serving(args):
+    """16 robots on 4 rooms maps, Poisson arrivals (20 Hz each), a 10 % map update before each
+    request, trees of U[100,1500] nodes. Served arm: the continuous-batching server, arrivals
+    replayed in real time for a bounded window, latency = submit -> results on the host. Plain
+    arm: the same requests in arrival order through lone mig_tree_eval calls, as a FIFO
+    single-server queue on the measured service times."""
+    import torch
+
+    import paper_2609_40297_gb300 as mig
+    import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    window = float(os.environ.get("MIG_SERVE_SECONDS", "2.0"))
+    maps_spec, pools, events, sensor = synth.serving_trace(seed=505 + 1000 * rank, duration_s=window)
+    rng = np.random.default_rng(77 + rank)
+    updates = [synth.map_update_box(rng, maps_spec[mi], 0.10) for (_, _, mi, _) in events]
+    ctx = mig.Context(local, stream=torch.cuda.Stream(local))
+
+    def fresh_maps():
+        return [mig.Map(ctx, m.grid, m.voxel_size, m.origin) for m in maps_spec]
+
+    # ---- warm-up (camera tables, kernels, allocator pools)
+    wm = fresh_maps()
+    t0_tree = pools[0][1][0]
+    for _ in range(args.warmup):
+        mig.tree_eval(wm[0], t0_tree.parent, t0_tree.pos, sensor)
+    for m in wm:
+        m.close()
+    # ---- served arm: real-time replay
+    maps = fresh_maps()
+    srv = mig.Server(ctx, arena_budget_bytes=8 << 30, max_inflight=64)
+    tickets = [None] * len(events)
+    start = time.perf_counter()
+
+    def submitter():
+        for i, (t_arr, rid, mi, ti) in enumerate(events):
+            delay = start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            (x0, y0, z0, dx, dy, dz), vox = updates[i]
+            srv.map_update(maps[mi], x0, y0, z0, vox)
+            tr = pools[rid][1][ti]
+            tickets[i] = srv.submit(maps[mi], tr.parent, tr.pos, sensor)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = []
+    for t, _ in tickets:
+        while not srv.poll(t, timeout_us=10_000_000):
+            pass
+        lat.append(srv.timing(t)["done_us"] / 1e3)
+    t_end = time.perf_counter()
+    clocks = sampler.stop()
+    served_results = [out for _, out in tickets]
+    srv.close()
+    for m in maps:
+        m.close()
+    served_span = t_end - start
+    # ---- plain arm: the same requests one by one (FIFO queue on measured service times)
+    maps = fresh_maps()
+    finish, lat_plain, service = 0.0, [], []
+    same = True
+    for i, (t_arr, rid, mi, ti) in enumerate(events):
+        (x0, y0, z0, dx, dy, dz), vox = updates[i]
+        tr = pools[rid][1][ti]
+        t0 = time.perf_counter()
+        maps[mi].update(x0, y0, z0, vox)
+        out = mig.tree_eval(maps[mi], tr.parent, tr.pos, sensor)
+        sv = time.perf_counter() - t0
+        service.append(sv)
+        finish = max(finish, t_arr) + sv
+        lat_plain.append((finish - t_arr) * 1e3)
+        same &= all(np.array_equal(out[k], served_results[i][k]) for k in ("abs", "marg", "yaw"))
+    for m in maps:
+        m.close()
+    ctx.close()
+    n = len(events)
+    plain_span = finish
+    rays = sum(pools[rid][1][ti].n for (_, rid, _, ti) in events) * sensor.yaw_bins * sensor.width * sensor.height
+    res = None
+    if rank == 0:
+        res = {"metric": METRIC, "value": ws * n / served_span, "unit": "replans/s", "n_gpus": ws,
+               "steps": n, "warmup": args.warmup, "ms_per_step": served_span / n * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 fixed point (u8 map)",
+               "data": "synthetic (seeded Poisson trace; stands in for robots replanning online)",
+               "config": {"workload": f"serving: 16 robots on 4 rooms maps 400x400x100 @0.1 m, Poisson 20 Hz each "
+                                      f"for {window:g} s of arrivals ({n} requests), trees U[100,1500] nodes, "
+                                      "160x120 rays, K=16, 10% map update before each request",
+                          "parallelism": f"replicas x{ws}"},
+               "served": {"replans_per_s": n / served_span, "rays_per_s": rays / served_span,
+                          "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}},
+               "plain": {"replans_per_s": n / plain_span, "rays_per_s": rays / plain_span,
+                         "latency_ms": {"p50": float(np.percentile(lat_plain, 50)),
+                                        "p99": float(np.percentile(lat_plain, 99))},
+                         "mean_service_ms": float(np.mean(service)) * 1e3},
+               "served_vs_plain_replans": (n / served_span) / (n / plain_span),
+               "results_identical_alone_vs_mix": bool(same),
+               "e2e": {"value": ws * n / served_span, "unit": "replans/s",
+                       "h2d_bytes_per_step": int(np.mean([pools[r][1][t].n * 16 for (_, r, _, t) in events])),
+                       "d2h_bytes_per_step": int(np.mean([pools[r][1][t].n * 12 for (_, r, _, t) in events]))},
+               "gpu_launches": None, "clocks": clocks}
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def cpu_baseline(workload, sample_depth=None, budget_s=20.0):
     """The oracle as it stands, on this host's cores, on a bounded, ancestor-closed sample of

@@ -52,6 +52,7 @@ typedef enum {
 
 typedef struct mig_ctx mig_ctx;
 typedef struct mig_map mig_map;
+typedef struct mig_server mig_server;
 
 /* Device memory provider. alloc returns device memory of `bytes` usable on `stream`
  * (NULL on failure); free releases it (stream-ordered). NULL allocator = cudaMallocAsync. */
@@ -217,6 +218,28 @@ typedef struct mig_trace_rec {
 mig_status mig_batch_trace(mig_ctx *ctx, int enable);
 mig_status mig_batch_trace_read(mig_ctx *ctx, mig_trace_rec *out, int cap, int *n);
 
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: continuous batching of replanning requests. Submitted trees wait in an admission
+ * queue until depth-buffer arena bytes (nodes * W * H * 4 plus counters) fit the budget, then
+ * join the device work of the requests already running; each request's results are the same
+ * as a lone mig_tree_eval on the map contents at submission time. The descriptor's host arrays
+ * are copied at submit; outputs are written when the request completes. A worker thread
+ * drives the device; submit and poll are thread-safe.
+ * mig_server_poll: MIG_OK = done (outputs written), MIG_EBUSY = not yet (timeout_us = 0),
+ * MIG_ETIMEOUT = still running after timeout_us, MIG_ENOTFOUND = unknown ticket.
+ * --------------------------------------------------------------------------------------- */
+mig_status mig_server_create(mig_ctx *ctx, size_t arena_budget_bytes, int max_inflight, mig_server **out);
+/* (a request whose bytes alone exceed the budget still runs when nothing else is in flight) */
+mig_status mig_server_submit(mig_server *srv, const mig_tree_desc *tree, uint64_t *ticket);
+mig_status mig_server_poll(mig_server *srv, uint64_t ticket, int64_t timeout_us);
+/* Map update routed through the server: applied after every request submitted before it and
+ * before every request submitted after it (requests keep their map snapshot). */
+mig_status mig_server_map_update(mig_server *srv, mig_map *map, int x0, int y0, int z0, int dx, int dy, int dz,
+                                 const uint8_t *host_voxels);
+/* Per-request timing (microseconds since submit): admitted, started on device, completed. */
+mig_status mig_server_timing(mig_server *srv, uint64_t ticket, double *admit_us, double *start_us, double *done_us);
+void mig_server_destroy(mig_server *srv);
 
 /* ---------------------------------------------------------------------------------------
  * Measurement (no counterpart in the paper; used by the benchmark's roofline figures).

@@ -32,7 +32,8 @@ EXPORTS = [
     "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device", "mig_tree_eval_device_noalloc",
     "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles", "mig_batch_set_timeout",
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read",
-    "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
+    "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
+    "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
 ]
 
 
@@ -374,3 +375,50 @@ def tree_eval_batch(ctx: Context, problems, maps, mode=MODE_MARGINAL):
                             o["abs"].ctypes.data, o["marg"].ctypes.data, o["yaw"].ctypes.data)
     check(lib().mig_tree_eval_batch(ctx.h, len(problems), descs))
     return outs
+
+
+class Server:
+    """mig_server: continuous batching of replanning requests (worker thread in the library)."""
+
+    def __init__(self, ctx: Context, arena_budget_bytes: int, max_inflight: int = 64):
+        out = C.c_void_p()
+        check(lib().mig_server_create(ctx.h, int(arena_budget_bytes), int(max_inflight), C.byref(out)))
+        self.h = out
+        self.ctx = ctx
+        self._keep = {}
+
+    def submit(self, m: Map, parent, pos, sensor, mode=MODE_MARGINAL):
+        """Returns (ticket, outputs dict); the outputs are filled when poll() returns True."""
+        parent = _host(parent, np.int32)
+        pos = _host(pos, np.float32).reshape(-1, 3)
+        n = parent.shape[0]
+        out = {k: np.zeros(n, np.int32) for k in ("abs", "marg", "yaw")}
+        d = TreeDesc(m.h.value, n, parent.ctypes.data, pos.ctypes.data, Sensor.of(sensor), int(mode),
+                     out["abs"].ctypes.data, out["marg"].ctypes.data, out["yaw"].ctypes.data)
+        t = C.c_uint64()
+        check(lib().mig_server_submit(self.h, C.byref(d), C.byref(t)))
+        self._keep[t.value] = out
+        return t.value, out
+
+    def map_update(self, m: Map, x0, y0, z0, box):
+        b = _host(box, np.uint8)
+        dz, dy, dx = b.shape
+        check(lib().mig_server_map_update(self.h, m.h, x0, y0, z0, dx, dy, dz, _ptr(b)))
+
+    def poll(self, ticket, timeout_us=0):
+        st = lib().mig_server_poll(self.h, C.c_uint64(ticket), int(timeout_us))
+        if st == MIG_OK:
+            return True
+        if st in (MIG_EBUSY, MIG_ETIMEOUT):
+            return False
+        check(st)
+
+    def timing(self, ticket):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        check(lib().mig_server_timing(self.h, C.c_uint64(ticket), C.byref(a), C.byref(b), C.byref(c)))
+        return {"admit_us": a.value, "start_us": b.value, "done_us": c.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mig_server_destroy(self.h)
+            self.h = None

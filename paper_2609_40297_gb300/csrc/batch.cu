@@ -34,9 +34,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ int load_acquire(const int *p) {
-    return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_acquire);
-}
 
 __device__ __forceinline__ int load_relaxed_i(const int *p) {
     return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_relaxed);

@@ -84,9 +84,12 @@ def test_batch_graph_replay_same_results(ctx, engine):
 
 
 def test_batch_wait_timeout_is_reported_and_recoverable(ctx):
+    """The persistent engine's device-side waits are bounded (engine 0)."""
     probs = _problems()[:3]
     maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in probs]
     args = [(p.tree.parent, p.tree.pos, p.sensor) for p in probs]
+    tw, th, cps, eng0 = ctx.get_tiles()
+    ctx.set_tiles(tw, th, cps, 0)
     try:
         good = mig.tree_eval_batch(ctx, args, maps)
         ctx.set_batch_timeout(200_000, debug_stall=True)  # 0.2 s; one level never completes
@@ -100,6 +103,7 @@ def test_batch_wait_timeout_is_reported_and_recoverable(ctx):
                 assert np.array_equal(x[k], y[k])
     finally:
         ctx.set_batch_timeout(5_000_000, debug_stall=False)
+        ctx.set_tiles(tw, th, cps, eng0)
         for m in maps:
             m.close()
 

@@ -107,7 +107,7 @@ def l2_flush_buffer(torch, dev):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.h"):
+    for f in ("kernels.cu", "kernels.h", "dev_path.cuh"):
         with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -503,7 +503,7 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(workload, sample_depth=None, budget_s=20.0):
+def cpu_baseline(workload, sample_depth=None, with_gap=False):
     """The oracle as it stands, on this host's cores, on a bounded, ancestor-closed sample of
     the workload (all nodes up to a depth), reported in the benchmark's unit."""
     import oracle
@@ -515,13 +515,24 @@ def cpu_baseline(workload, sample_depth=None, budget_s=20.0):
     mask = (d <= sample_depth).astype(np.uint8)
     m = int(mask.sum())
     t0 = time.perf_counter()
-    oracle.eval_tree(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent, prob.tree.pos, s,
-                     node_mask=mask)
+    db = oracle.eval_tree(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent, prob.tree.pos, s,
+                          node_mask=mask)
     dt = time.perf_counter() - t0
     rays = m * s.yaw_bins * s.width * s.height
-    return {"value": rays / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
-                      f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
+    out = {"value": rays / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
+                     f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
+    if with_gap:
+        # gap of the depth-buffer marginal gain to the exact one (Eq. 2 with the same yaws, Sec. V-A),
+        # both from the oracle on the same sample (the CUDA path is bit-identical to the oracle's DB part)
+        off, ids = oracle.visible_sets(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.pos, db["yaw"],
+                                       s, node_mask=mask)
+        ex = oracle.exact_dfs(prob.tree.parent, off, ids, prob.map.grid.size, node_mask=mask)
+        sel = mask.astype(bool)
+        rep = oracle.gap_report(d[sel], db["marg"][sel], ex[sel], abs_gain=db["abs"][sel])
+        rep["nodes"] = m
+        out["gap_to_exact"] = rep
+    return out
 
 
 def run_reference(args):
@@ -571,8 +582,9 @@ def main():
     ws, rank, _ = dist_env()
     if rank == 0 and res is not None:
         if ws == 1 and not args.no_cpu_baseline and args.workload in ("paper_scale", "tiny", "large"):
-            cb = cpu_baseline(args.workload)
+            cb = cpu_baseline(args.workload, with_gap=True)
             res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            res["gap_to_exact"] = cb.get("gap_to_exact")
         print(json.dumps(res))
 
 

@@ -199,8 +199,8 @@ def perlin_improved(x, y, z, perm):
 
 
 def world_terrain(rng, nx=800, ny=800, nz=200, target=0.12):
-    """Perlin heightfield terrain plus boxes; the terrain offset is bisected so that
-    `target` of all voxels are occupied."""
+    """Perlin heightfield terrain plus boxes; the terrain height scale is bisected (on a 4x column
+    subsample) so that about `target` of all voxels are occupied."""
     perm = rng.permutation(256).astype(np.int64)
     gy, gx = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
     h = np.zeros((ny, nx))
@@ -210,23 +210,21 @@ def world_terrain(rng, nx=800, ny=800, nz=200, target=0.12):
         amp *= 0.5
         freq *= 2.0
     h = (h - h.min()) / (h.max() - h.min() + 1e-12)  # [0,1]
-    boxes = np.zeros((nz, ny, nx), bool)
-    boxes = _boxes_until(rng, boxes.shape, 0.025, 8, 60, boxes)
+    boxes = _boxes_until(rng, (nz, ny, nx), 0.025, 8, 60)
     zc = np.arange(nz, dtype=np.float64)[:, None, None]
+    hs, bs = h[::4, ::4], boxes[:, ::4, ::4]
     lo, hi = 0.0, float(nz)
-    occ = None
+    mid = 0.5 * (lo + hi)
     for _ in range(30):
         mid = 0.5 * (lo + hi)
-        hz = mid * 0.5 + h * mid  # heights in voxels, min mid/2
-        occ = (zc < hz[None]) | boxes
-        f = occ.mean()
+        f = ((zc < (mid * 0.5 + hs * mid)[None]) | bs).mean()
         if abs(f - target) < 0.002:
             break
         if f < target:
             lo = mid
         else:
             hi = mid
-    return occ
+    return (zc < (mid * 0.5 + h * mid)[None]) | boxes
 
 
 # ----------------------------------------------------------------------------------

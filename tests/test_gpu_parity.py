@@ -210,3 +210,38 @@ def test_paper_scale_full_tree_bit_exact(ctx):
     got, ref = run_both(ctx, p.map.grid, p.map.voxel_size, p.map.origin, p.tree.parent, p.tree.pos, p.sensor,
                         depth=False)
     assert_same(got, ref, ("abs", "marg", "yaw", "cnt_abs", "cnt_marg"))
+
+
+def test_large_sampled_paths_bit_exact(ctx):
+    """The 2000-node, 800x800x200, 320x240-ray, K=36 workload: the whole tree on the device path
+    (the benchmark's launch configuration), checked against the oracle on every node of three
+    seeded root-to-leaf paths (an ancestor-closed subset the oracle evaluates exactly)."""
+    p = synth.large()
+    dev = torch.device("cuda:0")
+    m = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
+    try:
+        par = torch.from_numpy(p.tree.parent).to(dev)
+        pos = torch.from_numpy(p.tree.pos).to(dev)
+        outs = [torch.empty(p.tree.n, dtype=torch.int32, device=dev) for _ in range(3)]
+        mig.tree_eval_device(m, par, pos, p.sensor, int(p.tree.depth().max()), *outs)
+        ctx.sync()
+        got = [o.cpu().numpy() for o in outs]
+    finally:
+        m.close()
+    parent = p.tree.parent
+    is_leaf = np.ones(p.tree.n, bool)
+    is_leaf[parent[parent >= 0]] = False
+    depth = p.tree.depth()
+    rng = np.random.default_rng(3030)
+    deep = np.nonzero(is_leaf & (depth >= depth.max() - 2))[0]
+    mask = np.zeros(p.tree.n, np.uint8)
+    for leaf in rng.choice(deep, size=3, replace=False):
+        q = int(leaf)
+        while q >= 0:
+            mask[q] = 1
+            q = int(parent[q])
+    ref = oracle.eval_tree(p.map.grid, p.map.voxel_size, p.map.origin, parent, p.tree.pos, p.sensor, node_mask=mask)
+    sel = mask.astype(bool)
+    assert sel.sum() >= 16
+    for k, g in zip(("abs", "marg", "yaw"), got):
+        assert np.array_equal(g[sel], ref[k][sel]), k

@@ -198,6 +198,12 @@ typedef struct mig_tile_config {
 } mig_tile_config;
 mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg);
 mig_status mig_batch_get_tiles(mig_ctx *ctx, mig_tile_config *cfg);
+/* Autotuner: times each of the n_cands configurations on the sample batch (wall clock around the
+ * synchronous call, best of reps after a warm-up), fails with MIG_ECUDA if any candidate changes a
+ * result, and leaves the fastest configuration set on the context (also returned in *best;
+ * ms_out, nullable, receives n_cands times). The sample's output pointers are not used. */
+mig_status mig_autotune(mig_ctx *ctx, int n_trees, const mig_tree_desc *sample, int n_cands,
+                        const mig_tile_config *cands, int reps, mig_tile_config *best, double *ms_out);
 /* Time limit of every device-side dependency wait of the batched kernel (default 5 s); after
  * it the launch stops and returns MIG_ETIMEOUT, leaving the context usable. debug_stall != 0 is
  * a test hook that makes one level of the next batches never complete, so that the waits

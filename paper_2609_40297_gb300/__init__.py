@@ -31,7 +31,7 @@ EXPORTS = [
     "mig_default_resolution", "mig_tree_check",
     "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device", "mig_tree_eval_device_noalloc",
     "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles", "mig_batch_set_timeout",
-    "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read",
+    "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
     "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
 ]
@@ -137,6 +137,7 @@ def lib():
                 "mig_batch_set_timeout": (st, [p, C.c_int64, i]),
                 "mig_batch_graph_stats": (st, [p, p, p]),
                 "mig_batch_trace": (st, [p, i]),
+                "mig_autotune": (st, [p, i, p, i, p, i, p, p]),
                 "mig_batch_trace_read": (st, [p, p, i, p]),
                 "mig_server_create": (st, [p, C.c_size_t, i, p]),
                 "mig_server_submit": (st, [p, p, p]),
@@ -422,3 +423,53 @@ class Server:
         if getattr(self, "h", None):
             lib().mig_server_destroy(self.h)
             self.h = None
+
+
+DEFAULT_CANDIDATES = [(4, 16, 4, 1), (8, 8, 4, 1), (4, 8, 4, 1), (8, 16, 4, 1), (16, 16, 4, 1), (4, 16, 3, 1),
+                      (4, 16, 4, 0), (8, 8, 4, 0)]
+
+
+def autotune(ctx: Context, problems, maps, candidates=None, reps=2, cache_path=None):
+    """mig_autotune over (tile_w, tile_h, ctas_per_sm, engine) candidates on a sample batch of
+    (parent, pos, sensor) problems; the choice is cached in a JSON file keyed by GPU name and the
+    sample's ray-grid/yaw signature. Returns (best, {candidate: ms})."""
+    import json
+    cands = [tuple(c) for c in (candidates or DEFAULT_CANDIDATES)]
+    key = None
+    if cache_path:
+        import torch
+        sig = sorted({(int(Sensor.of(s).width), int(Sensor.of(s).height), int(Sensor.of(s).yaw_bins))
+                      for (_, _, s) in problems})
+        key = f"{torch.cuda.get_device_name(ctx.device)}|{sig}"
+        try:
+            with open(cache_path) as f:
+                hit = json.load(f).get(key)
+            if hit:
+                ctx.set_tiles(*hit["best"])
+                return tuple(hit["best"]), {tuple(map(int, k.split(","))): v for k, v in hit["ms"].items()}
+        except (OSError, ValueError):
+            pass
+    descs = (TreeDesc * len(problems))()
+    keep = []
+    for i, ((parent, pos, sensor), m) in enumerate(zip(problems, maps)):
+        parent = _host(parent, np.int32)
+        pos = _host(pos, np.float32).reshape(-1, 3)
+        keep += [parent, pos]
+        descs[i] = TreeDesc(m.h.value, parent.shape[0], parent.ctypes.data, pos.ctypes.data, Sensor.of(sensor), 0,
+                            None, None, None)
+    arr = (TileConfig * len(cands))(*[TileConfig(*c) for c in cands])
+    ms = (C.c_double * len(cands))()
+    best = TileConfig()
+    check(lib().mig_autotune(ctx.h, len(problems), descs, len(cands), arr, int(reps), C.byref(best), ms))
+    res = (best.tile_w, best.tile_h, best.ctas_per_sm, best.engine)
+    times = {c: ms[i] for i, c in enumerate(cands)}
+    if cache_path and key:
+        try:
+            with open(cache_path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+        data[key] = {"best": list(res), "ms": {",".join(map(str, c)): v for c, v in times.items()}}
+        with open(cache_path, "w") as f:
+            json.dump(data, f, indent=1)
+    return res, times

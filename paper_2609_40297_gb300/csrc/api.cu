@@ -490,7 +490,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
     }
     const int cap = ctx->num_sms * 16;
-    const int count_cap = ctx->num_sms * ctx->count_ctas;
+    const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     uint64_t n_count = 0, n_render = 0;
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
@@ -638,7 +638,7 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
     const int cap = ctx->num_sms * 16;
-    const int count_cap = ctx->num_sms * ctx->count_ctas;
+    const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {
         p.lvl = d;

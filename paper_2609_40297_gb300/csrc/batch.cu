@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstring>
 #include <memory>
@@ -428,7 +429,7 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
     mig_ctx::Batch *B = ctx->batch;
     if (!B->ctas) B->ctas = batch_ctas_per_sm();
-    const int grid = ctx->num_sms * B->ctas;
+    const int grid = ctx->num_sms * std::min(B->ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     // ---- graph: upload, zero counts and status, persistent kernel, download. The captured
     // graph bakes in the kernel parameters and the copy sizes: replay only while all match.
     GraphKey key;
@@ -616,7 +617,8 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
     for (int t = 0; t < T; ++t) order[t] = t;
     std::sort(order.begin(), order.end(), [&](int a, int c) { return items[a].plan.n > items[c].plan.n; });
     cudaStream_t s0 = ctx->stream;
-    const int cap = ctx->num_sms * 16, count_cap = ctx->num_sms * ctx->count_ctas;
+    const int cap = ctx->num_sms * 16;
+    const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(dev, host, up_bytes, cudaMemcpyHostToDevice, s0);
         if (e == cudaSuccess && zero_bytes) e = cudaMemsetAsync(dev + zero_start, 0, zero_bytes, s0);
@@ -799,5 +801,63 @@ extern "C" mig_status mig_batch_trace_read(mig_ctx *ctx, mig_trace_rec *out, int
     const int m = ctx->batch ? (int)ctx->batch->trace.size() : 0;
     *n = m;
     for (int i = 0; i < std::min(m, cap); ++i) out[i] = ctx->batch->trace[i];
+    return MIG_OK;
+}
+
+// Autotuner: times each candidate configuration on a sample batch (wall clock around the
+// synchronous batch call, best of `reps` after one warm-up), checks that every candidate gives
+// the same results, and leaves the fastest configuration set on the context.
+extern "C" mig_status mig_autotune(mig_ctx *ctx, int n_trees, const mig_tree_desc *sample, int n_cands,
+                                   const mig_tile_config *cands, int reps, mig_tile_config *best, double *ms_out) {
+    if (!ctx || n_trees < 1 || !sample || n_cands < 1 || !cands || reps < 1)
+        return fail(MIG_EINVAL, "autotune: invalid argument");
+    const mig_tile_config keep = ctx->tiles;
+    std::vector<std::vector<int32_t>> ref;
+    std::vector<mig_tree_desc> d(sample, sample + n_trees);
+    std::vector<std::vector<int32_t>> buf(n_trees);
+    for (int t = 0; t < n_trees; ++t) {
+        buf[t].assign(3 * (size_t)std::max(0, d[t].n_nodes), 0);
+        d[t].abs_gain = buf[t].data();
+        d[t].marg_gain = buf[t].data() + d[t].n_nodes;
+        d[t].best_yaw = buf[t].data() + 2 * (size_t)d[t].n_nodes;
+    }
+    int best_i = -1;
+    double best_ms = 1e300;
+    for (int c = 0; c < n_cands; ++c) {
+        mig_status st = mig_batch_set_tiles(ctx, &cands[c]);
+        if (st != MIG_OK) {
+            ctx->tiles = keep;
+            return st;
+        }
+        st = mig_tree_eval_batch(ctx, n_trees, d.data());  // warm-up (camera tables, graph capture)
+        if (st != MIG_OK) {
+            ctx->tiles = keep;
+            return st;
+        }
+        double ms = 1e300;
+        for (int r = 0; r < reps; ++r) {
+            const auto t0 = std::chrono::steady_clock::now();
+            st = mig_tree_eval_batch(ctx, n_trees, d.data());
+            const auto t1 = std::chrono::steady_clock::now();
+            if (st != MIG_OK) {
+                ctx->tiles = keep;
+                return st;
+            }
+            ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        }
+        if (ref.empty()) {
+            ref = buf;
+        } else if (ref != buf) {
+            ctx->tiles = keep;
+            return fail(MIG_ECUDA, "autotune: candidate " + std::to_string(c) + " changed the results");
+        }
+        if (ms_out) ms_out[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_i = c;
+        }
+    }
+    ctx->tiles = cands[best_i];
+    if (best) *best = cands[best_i];
     return MIG_OK;
 }

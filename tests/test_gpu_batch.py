@@ -120,3 +120,27 @@ def test_batch_empty_and_invalid(ctx):
         assert e.value.status == mig.MIG_EINVAL
     finally:
         m.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(ctx, tmp_path):
+    probs = _problems()[:4]
+    maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in probs]
+    keep = ctx.get_tiles()
+    try:
+        args = [(p.tree.parent, p.tree.pos, p.sensor) for p in probs]
+        before = mig.tree_eval_batch(ctx, args, maps)
+        cands = [(4, 16, 4, 1), (8, 8, 4, 1), (4, 16, 4, 0), (32, 8, 2, 0)]
+        cache = str(tmp_path / "tiles.json")
+        best, times = mig.autotune(ctx, args, maps, candidates=cands, reps=1, cache_path=cache)
+        assert best in cands and set(times) == set(cands) and ctx.get_tiles() == best
+        after = mig.tree_eval_batch(ctx, args, maps)
+        for x, y in zip(before, after):
+            for k in ("abs", "marg", "yaw"):
+                assert np.array_equal(x[k], y[k])
+        ctx.set_tiles(*keep)
+        best2, _ = mig.autotune(ctx, args, maps, candidates=cands, reps=1, cache_path=cache)  # cache hit
+        assert best2 == best and ctx.get_tiles() == best
+    finally:
+        ctx.set_tiles(*keep)
+        for m in maps:
+            m.close()

@@ -149,6 +149,21 @@ mig_status mig_tree_eval_device(mig_map *map, int n, const int32_t *parent, cons
                                 int32_t *best_yaw);
 
 /* ---------------------------------------------------------------------------------------
+ * Path scoring (Sec. III-C): traversal cost c(n) = c(Pa) + ||p_n - p_Pa|| (Eq. 3), objective
+ * o(n) = o(Pa) + g(n) exp(-lambda c(n)) (Eq. 4) with g(n) = gain_counts[n] * voxel_size^3 (m^3),
+ * and best_node = the lowest index with the largest objective (the branch the planner follows).
+ * Double precision. mig_tree_score takes host arrays and returns when done; the _device variant
+ * takes device arrays (gain_counts e.g. the marg_gain output of mig_tree_eval_device) and only
+ * enqueues on the context stream (a bad parent chain gives best_node = -1 and MIG_EINVAL at the
+ * next mig_ctx_sync). Errors: MIG_EINVAL (tree, voxel_size <= 0, lambda < 0), MIG_ENOMEM.
+ * --------------------------------------------------------------------------------------- */
+mig_status mig_tree_score(mig_ctx *ctx, int n, const int32_t *parent, const float *pos_m, const int32_t *gain_counts,
+                          double voxel_size_m, double lambda, double *cost, double *objective, int32_t *best_node);
+mig_status mig_tree_score_device(mig_ctx *ctx, int n, const int32_t *parent, const float *pos_m,
+                                 const int32_t *gain_counts, double voxel_size_m, double lambda, double *cost,
+                                 double *objective, int32_t *best_node);
+
+/* ---------------------------------------------------------------------------------------
  * Allocation-free evaluation. The paper has no counterpart; this entry point serves callers
  * that may not allocate device memory: a planner in a real-time control loop whose policy
  * forbids cudaMalloc after start-up (an allocation can stall or synchronise the device for an

@@ -30,6 +30,7 @@ EXPORTS = [
     "mig_map_create", "mig_map_update", "mig_map_read", "mig_map_destroy",
     "mig_default_resolution", "mig_tree_check",
     "mig_tree_eval", "mig_tree_eval_ex", "mig_tree_eval_device", "mig_tree_eval_device_noalloc",
+    "mig_tree_score", "mig_tree_score_device",
     "mig_tree_eval_batch", "mig_batch_set_tiles", "mig_batch_get_tiles", "mig_batch_set_timeout",
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
@@ -131,6 +132,8 @@ def lib():
                 "mig_tree_eval_ex": (st, [p, i, p, p, p, p, p, p, p]),
                 "mig_tree_eval_device": (st, [p, i, p, p, p, i, p, p, p]),
                 "mig_tree_eval_device_noalloc": (st, [p, i, p, p, p, i, p, p, p]),
+                "mig_tree_score": (st, [p, i, p, p, p, C.c_double, C.c_double, p, p, p]),
+                "mig_tree_score_device": (st, [p, i, p, p, p, C.c_double, C.c_double, p, p, p]),
                 "mig_tree_eval_batch": (st, [p, i, p]),
                 "mig_batch_set_tiles": (st, [p, p]),
                 "mig_batch_get_tiles": (st, [p, p]),
@@ -359,6 +362,20 @@ def tree_eval_device_noalloc(m: Map, parent_dev, pos_dev, sensor, max_depth, abs
                                              C.c_void_p(pos_dev.data_ptr()), C.byref(s), int(max_depth),
                                              C.c_void_p(abs_dev.data_ptr()), C.c_void_p(marg_dev.data_ptr()),
                                              C.c_void_p(yaw_dev.data_ptr())))
+
+
+def tree_score(ctx: Context, parent, pos, gain_counts, voxel_size, lam=0.5):
+    """mig_tree_score: (cost, objective, best node) of Eq. 3 and Eq. 4 on host arrays."""
+    parent = _host(parent, np.int32)
+    pos = _host(pos, np.float32).reshape(-1, 3)
+    gain = _host(gain_counts, np.int32)
+    n = parent.shape[0]
+    cost = np.zeros(n, np.float64)
+    obj = np.zeros(n, np.float64)
+    best = C.c_int32(-1)
+    check(lib().mig_tree_score(ctx.h, n, _ptr(parent), _ptr(pos), _ptr(gain), float(voxel_size), float(lam),
+                               _ptr(cost), _ptr(obj), C.byref(best)))
+    return cost, obj, best.value
 
 
 def tree_eval_batch(ctx: Context, problems, maps, mode=MODE_MARGINAL):

@@ -485,6 +485,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.work = (int32_t *)(dev + o_work);
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = mode;
+    p.max_anc = std::max(1, plan.max_depth);
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
@@ -637,6 +638,7 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     p.work = (int32_t *)(dev + o_work);
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
+    p.max_anc = std::max(1, max_depth);
     const int cap = ctx->num_sms * 16;
     const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));

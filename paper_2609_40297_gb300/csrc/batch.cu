@@ -82,7 +82,7 @@ __device__ __forceinline__ bool timed_out(const BatchParams &bp, unsigned long l
 #define MIG_BATCH_MINB MIG_COUNT_MINB
 #endif
 __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(const BatchParams bp) {
-    __shared__ AncRec s_anc[kWarps][MIG_MAX_DEPTH];
+    extern __shared__ AncRec s_anc_dyn[];  // bp.max_anc records per warp
     __shared__ unsigned long long s_q[kWarps][64];
     __shared__ int4 s_cam[kWarps][4];
     __shared__ HotVals s_hot[kWarps];
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(cons
                 __syncwarp();
                 cur_tree = sg.tree;
             }
-            count_chunk<false>(p, HotStaged{&s_hot[warp]}, l0, local, s_anc[warp], s_q[warp], s_cam[warp], lane);
+            count_chunk<false>(p, HotStaged{&s_hot[warp]}, l0, local, s_anc_dyn + warp * bp.max_anc, s_q[warp],
+                                   s_cam[warp], lane);
             int last = 0;
             if (lane == 0) {
                 __threadfence();
@@ -210,11 +211,17 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(cons
 
 }  // namespace
 
-void launch_batch(const BatchParams &bp, int grid, cudaStream_t s) { batch_kernel<<<grid, kWarps * 32, 0, s>>>(bp); }
+size_t batch_dyn_smem(int max_anc) { return (size_t)kWarps * (size_t)std::max(1, max_anc) * sizeof(AncRec); }
+
+void launch_batch(const BatchParams &bp, int grid, cudaStream_t s) {
+    batch_kernel<<<grid, kWarps * 32, batch_dyn_smem(bp.max_anc), s>>>(bp);
+}
 
 int batch_ctas_per_sm() {
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kWarps * 32, 0);
+    const size_t smem = batch_dyn_smem(MIG_MAX_DEPTH);  // the worst case
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kWarps * 32, smem);
     cudaGetLastError();
     return std::max(1, a);
 }
@@ -402,6 +409,7 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.mode = it.mode;
         p.lvl = 0;
         p.stats = nullptr;
+        p.max_anc = std::max(1, pl.max_depth);
         bt[t].p = p;
         bt[t].lvl_base = lvl_base[t];
         bt[t].n_levels = std::min(L, it.level_hi + 1);
@@ -425,6 +433,8 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
     bp.status = (int *)(dev + o_status);
     bp.trace = tracing ? (unsigned long long *)(dev + o_trace) : nullptr;
     bp.n_segs_total = (int)segs.size();
+    bp.max_anc = 1;
+    for (int t = 0; t < T; ++t) bp.max_anc = std::max(bp.max_anc, items[t].plan.max_depth);
     bp.timeout_ns = (unsigned long long)ctx->batch_timeout_ns;
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
     mig_ctx::Batch *B = ctx->batch;
@@ -598,6 +608,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.out_marg = p.out_abs + n;
         p.out_yaw = p.out_abs + 2 * (size_t)n;
         p.mode = it.mode;
+        p.max_anc = std::max(1, pl.max_depth);
         lp[t] = p;
     }
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();

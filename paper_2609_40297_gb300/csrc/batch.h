@@ -51,10 +51,12 @@ struct BatchParams {
     unsigned long long timeout_ns;
     unsigned long long *trace;  // NULL, or per segment (activated, completed) %globaltimer ns + kernel start
     int n_segs_total;
+    int max_anc;                // ancestor records per warp: the deepest tree's depth (dynamic smem)
     BatchTree trees[kBatchMaxTrees];
 };
 
 void launch_batch(const BatchParams &bp, int grid, cudaStream_t s);
+size_t batch_dyn_smem(int max_anc);
 int batch_ctas_per_sm();
 
 // Host-side description of one tree of a batch (or of a served request).

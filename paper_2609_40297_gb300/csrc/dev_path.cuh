@@ -356,6 +356,7 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
     int na = ar.y;
     if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
     else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
+    na = min(na, p.max_anc);  // the plan bounds depth by max_anc; this keeps the records in bounds
     __syncwarp();
     for (int t = lane; t < na; t += 32) {
         const int a = p.anc[ar.x + t];

@@ -20,7 +20,9 @@ using namespace dev;
 
 template <bool STATS>
 __global__ void __launch_bounds__(kWarps * 32, MIG_COUNT_MINB) count_kernel(const LevelParams p) {
-    __shared__ AncRec s_anc[kWarps][MIG_MAX_DEPTH];
+    // ancestor records: p.max_anc per warp, sized at launch from the tree's depth (dynamic shared
+    // memory), so that the rest of the unified L1/shared storage serves the voxel gathers
+    extern __shared__ AncRec s_anc_dyn[];
     __shared__ unsigned long long s_q[kWarps][64];
     __shared__ int4 s_cam[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -32,7 +34,7 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_COUNT_MINB) count_kernel(cons
         if (lane == 0) c = atomicAdd(p.work + p.lvl, 1);
         c = __shfl_sync(0xffffffffu, c, 0);
         if (c >= chunks) break;
-        count_chunk<STATS>(p, HotDirect{p}, l0, c, s_anc[warp], s_q[warp], s_cam[warp], lane);
+        count_chunk<STATS>(p, HotDirect{p}, l0, c, s_anc_dyn + warp * p.max_anc, s_q[warp], s_cam[warp], lane);
     }
 }
 
@@ -191,9 +193,12 @@ __global__ void plan_scatter_kernel(const DevPlanParams p) {
 
 }  // namespace
 
+size_t count_dyn_smem(int max_anc) { return (size_t)kWarps * (size_t)std::max(1, max_anc) * sizeof(AncRec); }
+
 void launch_count(const LevelParams &p, int grid, cudaStream_t s) {
-    if (p.stats) count_kernel<true><<<grid, kWarps * 32, 0, s>>>(p);
-    else count_kernel<false><<<grid, kWarps * 32, 0, s>>>(p);
+    const size_t smem = count_dyn_smem(p.max_anc);
+    if (p.stats) count_kernel<true><<<grid, kWarps * 32, smem, s>>>(p);
+    else count_kernel<false><<<grid, kWarps * 32, smem, s>>>(p);
 }
 
 size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz) {
@@ -209,8 +214,11 @@ size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz) {
 
 int count_ctas_per_sm() {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, count_kernel<false>, kWarps * 32, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel<true>, kWarps * 32, 0);
+    const size_t smem = count_dyn_smem(MIG_MAX_DEPTH);  // the worst case
+    cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, count_kernel<false>, kWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel<true>, kWarps * 32, smem);
     cudaGetLastError();
     return std::max(1, std::min(a, b));
 }

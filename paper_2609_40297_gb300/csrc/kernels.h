@@ -36,6 +36,7 @@ struct LevelParams {
     int mode;                   // mig_mode
     int lvl;
     unsigned long long *stats;  // NULL, or 8 counters (instrumented pass)
+    int max_anc;                // ancestor records per warp (>= the deepest node's depth, <= 64)
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);

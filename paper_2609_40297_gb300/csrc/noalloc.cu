@@ -205,6 +205,7 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
     p.stats = nullptr;
+    p.max_anc = std::max(1, max_depth);
     const int cap = ctx->num_sms * 16;
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {

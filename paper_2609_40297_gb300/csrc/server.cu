@@ -208,6 +208,7 @@ mig_status admit(mig_server *s, Request &r) {
     p.out_yaw = p.out_abs + 2 * (size_t)n;
     p.mode = r.mode;
     p.stats = nullptr;
+    p.max_anc = std::max(1, pl.max_depth);
     r.level = 0;
     return MIG_OK;
 }

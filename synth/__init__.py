@@ -133,7 +133,7 @@ def world_rooms(rng, nx=400, ny=400, nz=100, wall=2, slab=2, target=0.10):
         occ[:, :, c:c + wall] = True
         for a, b in zip(ybounds[:-1], ybounds[1:]):
             if b - a > 20:
-                w = int(rng.integers(10, 17))
+                w = min(int(rng.integers(10, 17)), b - a - 6)  # leaves room for the door's offset
                 s = int(rng.integers(a + 3, b - w - 2))
                 occ[slab:slab + door_h, s:s + w, c:c + wall] = False
     xbounds = [0] + xcuts + [nx]
@@ -141,7 +141,7 @@ def world_rooms(rng, nx=400, ny=400, nz=100, wall=2, slab=2, target=0.10):
         occ[:, c:c + wall, :] = True
         for a, b in zip(xbounds[:-1], xbounds[1:]):
             if b - a > 20:
-                w = int(rng.integers(10, 17))
+                w = min(int(rng.integers(10, 17)), b - a - 6)  # leaves room for the door's offset
                 s = int(rng.integers(a + 3, b - w - 2))
                 occ[slab:slab + door_h, c:c + wall, s:s + w] = False
     # pillars (full height) and low furniture boxes until the target fraction
@@ -452,6 +452,7 @@ def _batched_one(args):
     n = int(rng.integers(n_range[0], n_range[1] + 1))
     dmax = int(rng.integers(depth_range[0], depth_range[1] + 1))
     w, h = RAY_GRIDS[int(rng.integers(0, len(RAY_GRIDS)))]
+    n = min(n, sum(6 ** d for d in range(dmax + 1)) // 2)  # at most half a full 6-ary tree of that depth
     tree = rrt(rng, m, vps[0], n, dmax, 1.5, max_children=6, box=local_box(m, vps[0], 8.0, 1.0, 1.5))
     s = Sensor(90.0, 60.0, w, h, 6.0, 16, 0.0)
     m.truth = None  # not needed downstream; keeps the pickled result small
@@ -460,7 +461,7 @@ def _batched_one(args):
 
 def batched(seed_base=404, n_trees=64, n_range=(50, 2000), depth_range=(3, 15), workers=None):
     """64 independent problems on 64 seeded rooms maps (config-2 type, scans at 1 deg): tree sizes
-    U[50,2000], depth limits U[3,15], ray grids drawn from RAY_GRIDS, K=16, 6 m. Built in a pool
+    U[50,2000] (capped at half the nodes of a full 6-ary tree of the drawn depth), depth limits U[3,15], ray grids drawn from RAY_GRIDS, K=16, 6 m. Built in a pool
     of spawned worker processes when workers > 1."""
     jobs = [(seed_base + i, n_range, depth_range) for i in range(n_trees)]
     workers = workers if workers is not None else min(16, os.cpu_count() or 1)

@@ -245,3 +245,20 @@ def test_large_sampled_paths_bit_exact(ctx):
     assert sel.sum() >= 16
     for k, g in zip(("abs", "marg", "yaw"), got):
         assert np.array_equal(g[sel], ref[k][sel]), k
+
+
+def test_path_scoring_matches_oracle(ctx):
+    """Eq. 3 / Eq. 4 on the device against the fp64 oracle (libm exp vs CUDA exp: relative 1e-12);
+    the best node is an argmax of the oracle's objective up to that tolerance."""
+    from oracle.score import score_tree
+    for p in (synth.tiny(), synth.paper_scale()):
+        m = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
+        try:
+            g = mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor)
+        finally:
+            m.close()
+        cost, obj, best = mig.tree_score(ctx, p.tree.parent, p.tree.pos, g["marg"], p.map.voxel_size, 0.5)
+        c_ref, o_ref, b_ref = score_tree(p.tree.parent, p.tree.pos.astype(np.float64), g["marg"], p.map.voxel_size, 0.5)
+        assert np.allclose(cost, c_ref, rtol=1e-12, atol=1e-12)
+        assert np.allclose(obj, o_ref, rtol=1e-12, atol=0)
+        assert obj[best] >= o_ref.max() * (1 - 1e-12) and (best == b_ref or abs(o_ref[best] - o_ref[b_ref]) <= 1e-12 * o_ref.max())

@@ -453,3 +453,27 @@ def test_invalid_inputs_rejected(oracle_lib):
     g3[0, 0, 0] = 7
     with pytest.raises(oracle_lib.OracleError):
         oracle_lib.eval_tree(g3, v, o, par, pos, s)
+
+
+# ----------------------------------------------------------------------- path scoring
+def test_score_closed_forms():
+    """Eq. 3 and Eq. 4 on a straight chain with unit steps and equal gains: c(k) = k and
+    o(k) = g v^3 sum_{j<=k} exp(-lambda j) (a geometric series); a branch picks the larger sum."""
+    from oracle.score import score_tree
+    n, v, lam = 6, 0.2, 0.5
+    parent = np.arange(-1, n - 1)
+    pos = np.stack([np.arange(n, dtype=float), np.zeros(n), np.zeros(n)], 1)
+    gain = np.full(n, 1000)
+    cost, obj, best = score_tree(parent, pos, gain, v, lam)
+    assert np.allclose(cost, np.arange(n))
+    g = 1000 * v ** 3
+    expect = g * (1 - np.exp(-lam * np.arange(1, n + 1))) / (1 - np.exp(-lam))
+    assert np.allclose(obj, expect, rtol=1e-12)
+    assert best == n - 1
+    # a root with two children: a 3-4-5 step with a large gain beats a unit step with a small one
+    parent = np.array([-1, 0, 0])
+    pos = np.array([[0, 0, 0], [3, 4, 0], [1, 0, 0]], float)
+    cost, obj, best = score_tree(parent, pos, np.array([10, 500, 100]), 1.0, lam)
+    assert np.allclose(cost, [0, 5, 1])
+    assert np.isclose(obj[1], 10 + 500 * np.exp(-2.5)) and np.isclose(obj[2], 10 + 100 * np.exp(-0.5))
+    assert best == 2  # 100 e^-0.5 = 60.7 > 500 e^-2.5 = 41.0

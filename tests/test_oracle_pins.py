@@ -477,3 +477,15 @@ def test_score_closed_forms():
     assert np.allclose(cost, [0, 5, 1])
     assert np.isclose(obj[1], 10 + 500 * np.exp(-2.5)) and np.isclose(obj[2], 10 + 100 * np.exp(-0.5))
     assert best == 2  # 100 e^-0.5 = 60.7 > 500 e^-2.5 = 41.0
+    # lambda = 0: the objective is the plain path sum of gains (a star: root + own gain)
+    rng = np.random.default_rng(7)
+    parent = np.array([-1, 0, 0, 1, 1, 3])
+    pos = rng.normal(size=(6, 3))
+    gain = np.array([5, 7, 11, 13, 17, 19])
+    _, obj, best = score_tree(parent, pos, gain, 1.0, 0.0)
+    assert np.allclose(obj, [5, 12, 16, 25, 29, 44]) and best == 5
+    # equal objectives: the lowest index wins (two mirrored children of the root)
+    parent = np.array([-1, 0, 0])
+    pos = np.array([[0, 0, 0], [0, 1, 0], [0, -1, 0]], float)
+    _, obj, best = score_tree(parent, pos, np.array([1, 9, 9]), 1.0, lam)
+    assert obj[1] == obj[2] and best == 1

@@ -37,12 +37,15 @@ void DeviceAllocator::free(void *p, size_t bytes, cudaStream_t s) {
     else cudaFreeAsync(p, s);
 }
 
+extern "C" void mig_batch_drop_graphs(mig_ctx *ctx);  // batch.cu
+
 mig_status ctx_workspace(mig_ctx *ctx, size_t bytes, void **out) {
     if (ctx->ws.bytes < bytes) {
+        const size_t want = std::max(bytes, ctx->ws.bytes + ctx->ws.bytes / 2);
+        if (ctx->ws.ptr) mig_batch_drop_graphs(ctx);  // captured graphs copy into the old buffer
         ctx->alloc.free(ctx->ws.ptr, ctx->ws.bytes, ctx->stream);
         ctx->ws.ptr = nullptr;
         ctx->ws.bytes = 0;
-        const size_t want = std::max(bytes, ctx->ws.bytes + ctx->ws.bytes / 2);
         void *p = ctx->alloc.alloc(want, ctx->stream);
         if (!p) {
             p = ctx->alloc.alloc(bytes, ctx->stream);
@@ -59,13 +62,14 @@ mig_status ctx_workspace(mig_ctx *ctx, size_t bytes, void **out) {
 
 mig_status ctx_pinned(mig_ctx *ctx, size_t bytes, void **out) {
     if (ctx->pinned_bytes < bytes) {
+        const size_t want = std::max({bytes, (size_t)1 << 20, 2 * ctx->pinned_bytes});
         if (ctx->pinned) {
+            mig_batch_drop_graphs(ctx);  // captured graphs copy from and to the old buffer
             cudaStreamSynchronize(ctx->stream);
             cudaFreeHost(ctx->pinned);
         }
         ctx->pinned = nullptr;
         ctx->pinned_bytes = 0;
-        const size_t want = std::max(bytes, (size_t)1 << 20);
         if (cudaHostAlloc(&ctx->pinned, want, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             ctx->pinned = nullptr;

@@ -83,7 +83,7 @@ __device__ __forceinline__ bool timed_out(const BatchParams &bp, unsigned long l
 #endif
 __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(const BatchParams bp) {
     extern __shared__ AncRec s_anc_dyn[];  // bp.max_anc records per warp
-    __shared__ unsigned long long s_q[kWarps][64];
+    __shared__ unsigned long long s_q[kWarps][kQueue];
     __shared__ int4 s_cam[kWarps][4];
     __shared__ HotVals s_hot[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -705,6 +705,25 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
 }
 
 }  // namespace
+
+// Destroys the captured batch graphs of both engines. Called before the context frees a buffer
+// that their copy nodes reference (the device workspace, the pinned staging buffer): a graph must
+// not outlive memory it copies to or from, even when a later allocation returns the same address
+// and the replay key would match again.
+extern "C" void mig_batch_drop_graphs(mig_ctx *ctx) {
+    if (!ctx || !ctx->batch) return;
+    mig_ctx::Batch *B = ctx->batch;
+    if (!B->exec && !B->sexec) return;
+    cudaStreamSynchronize(ctx->stream);  // every batch launch is on the context stream
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->sexec) cudaGraphExecDestroy(B->sexec);
+    if (B->sgraph) cudaGraphDestroy(B->sgraph);
+    B->exec = B->sexec = nullptr;
+    B->graph = B->sgraph = nullptr;
+    std::memset(&B->key, 0, sizeof(B->key));
+    B->skey.clear();
+}
 
 extern "C" void mig_batch_release(mig_ctx *ctx) {
     if (!ctx || !ctx->batch) return;

@@ -21,6 +21,14 @@
 #ifndef MIG_BRANCHLESS
 #define MIG_BRANCHLESS 1
 #endif
+// 1 = the step's axis from two cross-product comparisons (x against y, the earlier against z)
+// instead of three; the same lexicographic (t, axis) minimum.
+#ifndef MIG_DDA_SEQ
+#define MIG_DDA_SEQ 1
+#endif
+#if MIG_DDA_SEQ && !MIG_BRANCHLESS
+#error "MIG_DDA_SEQ needs MIG_BRANCHLESS"
+#endif
 // 1 = the batched ancestor test is an out-of-line call (its register needs do not add to the
 // DDA loop's), 0 = inlined.
 #ifndef MIG_OBS_NOINLINE
@@ -30,6 +38,14 @@
 // from the warp's shared-memory slot at each use instead of being held in registers.
 #ifndef MIG_CAM_SMEM
 #define MIG_CAM_SMEM 1
+#endif
+// Count loop: each lane runs MIG_COUNT_BLOCK DDA steps of its ray between two warp-wide
+// exchanges (ray refill, sample queue); 0 = one exchange per step.
+#ifndef MIG_COUNT_BLOCK
+#define MIG_COUNT_BLOCK 4
+#endif
+#ifndef MIG_COUNT_UNROLL
+#define MIG_COUNT_UNROLL 1
 #endif
 // Minimum resident count-kernel CTAs per SM requested from the register allocator.
 #ifndef MIG_COUNT_MINB
@@ -135,13 +151,25 @@ __device__ __forceinline__ void ray_dir(const int4 b, int ck, int sk, int &dx, i
 // DEPTH: also report the entry face distance / speed (ne / ade) of the new voxel.
 template <bool DEPTH>
 __device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) {
+#if MIG_DDA_SEQ
+    // lexicographic minimum of (t, axis) in two comparisons: the earlier of x and y (ties x), then
+    // that one against z (ties to it); t_a = n_a / ad_a compared by cross products
+    const bool xly = (uint64_t)r.nx * r.ady <= (uint64_t)r.ny * r.adx;
+    const uint32_t nw = xly ? r.nx : r.ny, aw = xly ? r.adx : r.ady;
+    const bool bz = !((uint64_t)nw * r.adz <= (uint64_t)r.nz * aw);
+    const bool bx = !bz && xly;
+    const bool by = !bz && !xly;
+#else
     const uint64_t xy = (uint64_t)r.nx * r.ady, yx = (uint64_t)r.ny * r.adx;
     const uint64_t xz = (uint64_t)r.nx * r.adz, zx = (uint64_t)r.nz * r.adx;
     const uint64_t yz = (uint64_t)r.ny * r.adz, zy = (uint64_t)r.nz * r.ady;
+#endif
 #if MIG_BRANCHLESS
+#if !MIG_DDA_SEQ
     const bool bx = (xy <= yx) && (xz <= zx);
     const bool by = !bx && (yz <= zy);
     const bool bz = !bx && !by;
+#endif
     const int rem = bx ? r.rx : (by ? r.ry : r.rz);
     if (rem == 0) return false;
     if constexpr (DEPTH) {
@@ -220,6 +248,11 @@ __device__ __forceinline__ void decode_item(const LevelParams &p, int item, int 
 // tested against the ancestors' depth buffers with all 32 lanes at once (Sec. IV-B), so the
 // rare, long ancestor test never runs one lane at a time.
 constexpr int kWarps = 8;
+constexpr int kCountBlock = MIG_COUNT_BLOCK > 0 ? MIG_COUNT_BLOCK : 1;
+// per-warp sample queue: the main queue (< 32 carried + 32 x kCountBlock appended at an exchange)
+// followed by 32 x kCountBlock private slots (one column per lane)
+constexpr int kQueueMain = 32 * (kCountBlock + 1);
+constexpr int kQueue = kQueueMain + 32 * kCountBlock;
 
 struct AncRec {
     int px, py, pz, yaw;
@@ -400,6 +433,119 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
     RayIn r;
     uint32_t ne = 0, ade = 1;
     uint32_t st_steps = 0, st_unk = 0, st_anc = 0, st_reads = 0, st_rays = 0;
+#if MIG_COUNT_BLOCK > 0
+    // Block-synchronous loop. Between two warp-wide exchanges every lane runs kCountBlock DDA steps
+    // of its own ray with no vote; an owned sample goes to the lane's private slots of the queue
+    // (pend[i * 32 + lane]). At the exchange, the warp refills ended rays, appends the pending
+    // samples to the shared queue in lane order (prefix sum of the per-lane counts) and tests every
+    // full batch of 32 against the ancestors.
+    unsigned long long *pend = q + kQueueMain;
+    for (;;) {
+        const unsigned need = __ballot_sync(0xffffffffu, !have);
+        if (need == 0xffffffffu && next >= tile_rays) break;
+        if (need && next < tile_rays) {
+            const int idx = next + __popc(need & lt_mask);
+            next += __popc(need);
+            if (!have && idx < tile_rays) {
+                ti = tx0 + idx % hp.tile_w();
+                tj = ty0 + idx / hp.tile_w();
+                if (ti < hp.W() && tj < hp.H()) {
+                    const int4 b = hp.body()[tj * hp.W() + ti];
+                    int dx, dy, dz;
+#if MIG_CAM_SMEM
+                    const int4 c3 = lds128(cam + 3), c0 = lds128(cam);
+                    ray_dir(b, c3.x, c3.y, dx, dy, dz);
+                    ray_init_dims(r, hp.nx(), hp.ny(), hp.nz(), p.grid, c0.x, c0.y, c0.z, dx, dy, dz, hp.Tq());
+#else
+                    ray_dir(b, ck, sk, dx, dy, dz);
+                    ray_init_dims(r, hp.nx(), hp.ny(), hp.nz(), p.grid, nd.x, nd.y, nd.z, dx, dy, dz, hp.Tq());
+#endif
+                    have = true;
+                    if constexpr (STATS) ++st_rays;
+                }
+            }
+        }
+        int cnt = 0;
+#if MIG_COUNT_UNROLL
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
+        for (int sidx = 0; sidx < kCountBlock; ++sidx) {
+            if (have) {
+                const uint8_t code = __ldg(hp.g() + ray_addr(r, p.grid));
+                if constexpr (STATS) ++st_steps;
+                if (code == kOcc) {
+                    have = false;
+                } else {
+                    if (code == kUnknown) {
+                        if constexpr (STATS) ++st_unk;
+                        // owner test: centre of this voxel projects into pixel (ti, tj)
+#if MIG_CAM_SMEM
+                        const int4 c0 = lds128(cam), c1 = lds128(cam + 1);
+                        const int rx = (r.vx << 16) + 32768 - c0.x;
+                        const int ry = (r.vy << 16) + 32768 - c0.y;
+                        const int rz = (r.vz << 16) + 32768 - c0.z;
+                        const int64_t Z = (int64_t)c0.w * rx + (int64_t)c1.x * ry + (int64_t)c1.y * rz;
+                        const int64_t U = (int64_t)c1.z * rx + (int64_t)c1.w * ry + (int64_t)lds128(cam + 2).x * rz;
+#else
+                        const int rx = (r.vx << 16) + 32768 - nd.x;
+                        const int ry = (r.vy << 16) + 32768 - nd.y;
+                        const int rz = (r.vz << 16) + 32768 - nd.z;
+                        const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * rz;
+                        const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * rz;
+#endif
+                        const int64_t iZ = (int64_t)ti * Z;
+                        if (Z > 0 && U >= iZ && U < iZ + Z) {
+#if MIG_CAM_SMEM
+                            const int4 c2 = lds128(cam + 2);
+                            const int64_t V = (int64_t)c2.y * rx + (int64_t)c2.z * ry + (int64_t)c2.w * rz;
+#else
+                            const int64_t V = (int64_t)mv0 * rx + (int64_t)mv1 * ry + (int64_t)mv2 * rz;
+#endif
+                            const int64_t jZ = (int64_t)tj * Z;
+                            if (V >= jZ && V < jZ + Z) {
+                                pend[cnt * 32 + lane] = (unsigned long long)(uint32_t)r.vx |
+                                                        ((unsigned long long)(uint32_t)r.vy << 16) |
+                                                        ((unsigned long long)(uint32_t)r.vz << 32);
+                                ++cnt;
+                            }
+                        }
+                    }
+                    have = ray_step<false>(r, ne, ade);
+                }
+            }
+        }
+        const int tot = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        if (tot) {
+            c_abs += cnt;
+            int off = cnt;  // inclusive prefix sum over the lanes, then exclusive
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, off, d);
+                if (lane >= d) off += v;
+            }
+            off = qn + off - cnt;
+            for (int i = 0; i < cnt; ++i) q[off + i] = pend[i * 32 + lane];
+            qn += tot;
+            if (qn >= 32) {  // full batches: every lane tests one sample (Sec. IV-B)
+                __syncwarp();
+                int base = 0;
+                do {
+                    const unsigned long long sm = q[base + lane];
+                    const int sx = (int)(sm & 0xFFFF), sy = (int)((sm >> 16) & 0xFFFF), sz = (int)(sm >> 32);
+                    c_mrg += !observed<STATS>(hp, anc, na, sx, sy, sz, st_anc, st_reads);
+                    base += 32;
+                } while (qn - base >= 32);
+                const int left = qn - base;
+                const unsigned long long keep = lane < left ? q[base + lane] : 0ull;
+                __syncwarp();
+                if (lane < left) q[lane] = keep;
+                qn = left;
+            }
+        }
+    }
+#else
     for (;;) {
         // lanes without a ray take the chunk's next rays in order (neighbouring pixels)
         const unsigned need = __ballot_sync(0xffffffffu, !have);
@@ -488,6 +634,7 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
             }
         }
     }
+#endif
     // the last, partial batch
     __syncwarp();
     if (lane < qn) {

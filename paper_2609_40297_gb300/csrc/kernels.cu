@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_COUNT_MINB) count_kernel(cons
     // ancestor records: p.max_anc per warp, sized at launch from the tree's depth (dynamic shared
     // memory), so that the rest of the unified L1/shared storage serves the voxel gathers
     extern __shared__ AncRec s_anc_dyn[];
-    __shared__ unsigned long long s_q[kWarps][64];
+    __shared__ unsigned long long s_q[kWarps][kQueue];
     __shared__ int4 s_cam[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int l0 = p.level_off[p.lvl];

@@ -144,3 +144,31 @@ def test_autotune_picks_a_candidate_and_keeps_results(ctx, tmp_path):
         ctx.set_tiles(*keep)
         for m in maps:
             m.close()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_batch_graph_survives_buffer_regrowth(ctx, engine):
+    """A captured batch graph copies through the context's pinned staging buffer and device
+    workspace. When a larger call regrows them, the old graph is dropped, never replayed into freed
+    memory: the small batch recaptures and returns the same results."""
+    small = _problems()[:3]
+    big = [synth.random_small(60 + i, n_nodes=2000, max_depth=12) for i in range(20)]  # > 1 MiB of plan data
+    maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in small + big]
+    tw, th, cps, eng0 = ctx.get_tiles()
+    ctx.set_tiles(tw, th, cps, engine)
+    try:
+        args = [(p.tree.parent, p.tree.pos, p.sensor) for p in small]
+        a = mig.tree_eval_batch(ctx, args, maps[:3])
+        a2 = mig.tree_eval_batch(ctx, args, maps[:3])  # a replay of the captured graph
+        cap0, _ = ctx.graph_stats()
+        mig.tree_eval_batch(ctx, [(p.tree.parent, p.tree.pos, p.sensor) for p in big], maps[3:])
+        b = mig.tree_eval_batch(ctx, args, maps[:3])
+        cap1, _ = ctx.graph_stats()
+        assert cap1 >= cap0 + 1  # the big batch and the small one were captured anew
+        for x, y, z in zip(a, a2, b):
+            for k in ("abs", "marg", "yaw"):
+                assert np.array_equal(x[k], y[k]) and np.array_equal(x[k], z[k])
+    finally:
+        ctx.set_tiles(tw, th, cps, eng0)
+        for m in maps:
+            m.close()

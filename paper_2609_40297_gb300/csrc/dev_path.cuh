@@ -17,18 +17,6 @@
 #ifndef MIG_LAYOUT
 #define MIG_LAYOUT 1
 #endif
-// 1 = branch-free axis step (selects), 0 = three-way branch.
-#ifndef MIG_BRANCHLESS
-#define MIG_BRANCHLESS 1
-#endif
-// 1 = the step's axis from two cross-product comparisons (x against y, the earlier against z)
-// instead of three; the same lexicographic (t, axis) minimum.
-#ifndef MIG_DDA_SEQ
-#define MIG_DDA_SEQ 1
-#endif
-#if MIG_DDA_SEQ && !MIG_BRANCHLESS
-#error "MIG_DDA_SEQ needs MIG_BRANCHLESS"
-#endif
 // 1 = the batched ancestor test is an out-of-line call (its register needs do not add to the
 // DDA loop's), 0 = inlined.
 #ifndef MIG_OBS_NOINLINE
@@ -69,58 +57,70 @@ __device__ __forceinline__ uint32_t voxel_addr(const GridView &G, int x, int y, 
 }
 
 // Per-axis DDA set-up (Sec. IV-B, Amanatides-Woo). n = distance to the next face (Q16),
-// ad = |d| (Q30); rem = number of face crossings along this axis that stay inside the grid
-// and start before the range T (crossing k is at t = (n + k 2^16) / ad, allowed iff < T).
+// ad = |d| (Q30), s = step sign, l = face limit: crossing k along this axis is at n + k 2^16 and
+// is taken iff it stays inside the grid and starts before the range T (t = (n + k 2^16) / ad < T),
+// i.e. iff the current n is below l. An axis with d = 0 is never stepped (l = n); it still gets
+// s = 1 and n = distance to the upper face, so that s (n - 2^15) is the voxel-centre offset on
+// every axis (see voxel_offset).
 __device__ __forceinline__ void axis_init(int P, int d, int N, int64_t Tq, int &v, uint32_t &n, uint32_t &ad, int &s,
-                                          int &rem) {
+                                          uint32_t &l) {
     v = P >> 16;
     int grid_rem;
-    if (d > 0) {
-        s = 1;
-        ad = (uint32_t)d;
-        n = (uint32_t)(((v + 1) << 16) - P);
-        grid_rem = N - 1 - v;
-    } else if (d < 0) {
+    if (d < 0) {
         s = -1;
         ad = (uint32_t)(-d);
         n = (uint32_t)(P - (v << 16));
         grid_rem = v;
     } else {
-        s = 0;
-        ad = 0;
-        n = kQ16;
-        rem = 0;
-        return;
+        s = 1;
+        ad = (uint32_t)d;
+        n = (uint32_t)(((v + 1) << 16) - P);
+        grid_rem = N - 1 - v;
+        if (d == 0) {
+            l = n;
+            return;
+        }
     }
     const uint64_t lim = ((uint64_t)Tq * ad + ((1ull << 30) - 1)) >> 30;  // n >= lim  <=>  t >= T
     const int64_t range_rem = (n >= lim) ? 0 : (int64_t)((lim - n + (kQ16 - 1)) >> 16);
-    rem = (int)min((int64_t)grid_rem, range_rem);
+    l = n + ((uint32_t)min((int64_t)grid_rem, range_rem) << 16);
 }
 
+// DDA state of one ray. The current voxel is not stored: along an axis with step sign s, the
+// centre of the current voxel lies s (n - 2^15) (Q16) from the ray origin, because n is the
+// distance from the origin to the voxel's far face along the ray's direction of travel.
 struct RayIn {
-    int vx, vy, vz;
-    uint32_t nx, ny, nz, adx, ady, adz;
-    int sx, sy, sz, rx, ry, rz;
+    uint32_t nx, ny, nz, adx, ady, adz, lx, ly, lz;
+    int sx, sy, sz;
 #if MIG_LAYOUT == 1
     uint32_t addr;
     int dax, day, daz;  // signed address strides of one step along each axis
+#else
+    int vx, vy, vz;
 #endif
 };
 
+// Q16 offset, along one axis, of the current voxel's centre from the ray origin.
+__device__ __forceinline__ int voxel_offset(uint32_t n, int s) { return s * (int)(n - 32768u); }
+
 __device__ __forceinline__ void ray_init_dims(RayIn &r, int gnx, int gny, int gnz, const GridView &G, int Px, int Py,
                                               int Pz, int dx, int dy, int dz, int64_t Tq) {
-    axis_init(Px, dx, gnx, Tq, r.vx, r.nx, r.adx, r.sx, r.rx);
-    axis_init(Py, dy, gny, Tq, r.vy, r.ny, r.ady, r.sy, r.ry);
-    axis_init(Pz, dz, gnz, Tq, r.vz, r.nz, r.adz, r.sz, r.rz);
+    int vx, vy, vz;
+    axis_init(Px, dx, gnx, Tq, vx, r.nx, r.adx, r.sx, r.lx);
+    axis_init(Py, dy, gny, Tq, vy, r.ny, r.ady, r.sy, r.ly);
+    axis_init(Pz, dz, gnz, Tq, vz, r.nz, r.adz, r.sz, r.lz);
 #if MIG_LAYOUT == 1
     (void)G;
-    r.addr = ((uint32_t)r.vz * (uint32_t)gny + (uint32_t)r.vy) * (uint32_t)gnx + (uint32_t)r.vx;
+    r.addr = ((uint32_t)vz * (uint32_t)gny + (uint32_t)vy) * (uint32_t)gnx + (uint32_t)vx;
     r.dax = r.sx;
     r.day = r.sy * gnx;
     r.daz = r.sz * gnx * gny;
 #else
     (void)gnx;
     (void)gny;
+    r.vx = vx;
+    r.vy = vy;
+    r.vz = vz;
 #endif
 }
 
@@ -151,78 +151,30 @@ __device__ __forceinline__ void ray_dir(const int4 b, int ck, int sk, int &dx, i
 // DEPTH: also report the entry face distance / speed (ne / ade) of the new voxel.
 template <bool DEPTH>
 __device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) {
-#if MIG_DDA_SEQ
     // lexicographic minimum of (t, axis) in two comparisons: the earlier of x and y (ties x), then
     // that one against z (ties to it); t_a = n_a / ad_a compared by cross products
     const bool xly = (uint64_t)r.nx * r.ady <= (uint64_t)r.ny * r.adx;
-    const uint32_t nw = xly ? r.nx : r.ny, aw = xly ? r.adx : r.ady;
+    const uint32_t nw = xly ? r.nx : r.ny, aw = xly ? r.adx : r.ady, lw = xly ? r.lx : r.ly;
     const bool bz = !((uint64_t)nw * r.adz <= (uint64_t)r.nz * aw);
     const bool bx = !bz && xly;
     const bool by = !bz && !xly;
-#else
-    const uint64_t xy = (uint64_t)r.nx * r.ady, yx = (uint64_t)r.ny * r.adx;
-    const uint64_t xz = (uint64_t)r.nx * r.adz, zx = (uint64_t)r.nz * r.adx;
-    const uint64_t yz = (uint64_t)r.ny * r.adz, zy = (uint64_t)r.nz * r.ady;
-#endif
-#if MIG_BRANCHLESS
-#if !MIG_DDA_SEQ
-    const bool bx = (xy <= yx) && (xz <= zx);
-    const bool by = !bx && (yz <= zy);
-    const bool bz = !bx && !by;
-#endif
-    const int rem = bx ? r.rx : (by ? r.ry : r.rz);
-    if (rem == 0) return false;
+    const uint32_t nc = bz ? r.nz : nw;
+    if (nc >= (bz ? r.lz : lw)) return false;
     if constexpr (DEPTH) {
-        ne = bx ? r.nx : (by ? r.ny : r.nz);
-        ade = bx ? r.adx : (by ? r.ady : r.adz);
+        ne = nc;
+        ade = bz ? r.adz : aw;
     }
-    r.rx -= bx;
-    r.ry -= by;
-    r.rz -= bz;
     r.nx += bx ? kQ16 : 0u;
     r.ny += by ? kQ16 : 0u;
     r.nz += bz ? kQ16 : 0u;
+#if MIG_LAYOUT == 1
+    r.addr += bx ? r.dax : (by ? r.day : r.daz);
+#else
     r.vx += bx ? r.sx : 0;
     r.vy += by ? r.sy : 0;
     r.vz += bz ? r.sz : 0;
-#if MIG_LAYOUT == 1
-    r.addr += bx ? r.dax : (by ? r.day : r.daz);
 #endif
     return true;
-#else
-    if (xy <= yx && xz <= zx) {
-        if (r.rx == 0) return false;
-        --r.rx;
-        ne = r.nx;
-        ade = r.adx;
-        r.nx += kQ16;
-        r.vx += r.sx;
-#if MIG_LAYOUT == 1
-        r.addr += r.dax;
-#endif
-    } else if (yz <= zy) {
-        if (r.ry == 0) return false;
-        --r.ry;
-        ne = r.ny;
-        ade = r.ady;
-        r.ny += kQ16;
-        r.vy += r.sy;
-#if MIG_LAYOUT == 1
-        r.addr += r.day;
-#endif
-    } else {
-        if (r.rz == 0) return false;
-        --r.rz;
-        ne = r.nz;
-        ade = r.adz;
-        r.nz += kQ16;
-        r.vz += r.sz;
-#if MIG_LAYOUT == 1
-        r.addr += r.daz;
-#endif
-    }
-    return true;
-#endif
 }
 
 // Depth (Q16.16 voxel units, camera z) of the entry point t_e = ne / ade of the hit voxel, or
@@ -376,6 +328,14 @@ __device__ __forceinline__ int4 lds128(const int4 *ptr) {
     return v;
 }
 
+// Queue key of an owned sample: voxel coordinates (16 bits each) recovered from the voxel-centre
+// offsets (Q16) and the ray origin o (Q16, o.x / o.y / o.z).
+__device__ __forceinline__ unsigned long long sample_key(int rx, int ry, int rz, const int4 o) {
+    const uint32_t x = (uint32_t)(rx + o.x - 32768) >> 16, y = (uint32_t)(ry + o.y - 32768) >> 16,
+                   z = (uint32_t)(rz + o.z - 32768) >> 16;
+    return (unsigned long long)x | ((unsigned long long)y << 16) | ((unsigned long long)z << 32);
+}
+
 // cam: the warp's 4 x int4 shared slot, (px py pz mz0) (mz1 mz2 mu0 mu1) (mu2 mv0 mv1 mv2) (ck sk - -)
 template <bool STATS, class HOT>
 __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp, int l0, int c, AncRec *anc,
@@ -481,17 +441,14 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
                     if (code == kUnknown) {
                         if constexpr (STATS) ++st_unk;
                         // owner test: centre of this voxel projects into pixel (ti, tj)
+                        const int rx = voxel_offset(r.nx, r.sx);
+                        const int ry = voxel_offset(r.ny, r.sy);
+                        const int rz = voxel_offset(r.nz, r.sz);
 #if MIG_CAM_SMEM
                         const int4 c0 = lds128(cam), c1 = lds128(cam + 1);
-                        const int rx = (r.vx << 16) + 32768 - c0.x;
-                        const int ry = (r.vy << 16) + 32768 - c0.y;
-                        const int rz = (r.vz << 16) + 32768 - c0.z;
                         const int64_t Z = (int64_t)c0.w * rx + (int64_t)c1.x * ry + (int64_t)c1.y * rz;
                         const int64_t U = (int64_t)c1.z * rx + (int64_t)c1.w * ry + (int64_t)lds128(cam + 2).x * rz;
 #else
-                        const int rx = (r.vx << 16) + 32768 - nd.x;
-                        const int ry = (r.vy << 16) + 32768 - nd.y;
-                        const int rz = (r.vz << 16) + 32768 - nd.z;
                         const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * rz;
                         const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * rz;
 #endif
@@ -505,9 +462,12 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
 #endif
                             const int64_t jZ = (int64_t)tj * Z;
                             if (V >= jZ && V < jZ + Z) {
-                                pend[cnt * 32 + lane] = (unsigned long long)(uint32_t)r.vx |
-                                                        ((unsigned long long)(uint32_t)r.vy << 16) |
-                                                        ((unsigned long long)(uint32_t)r.vz << 32);
+#if MIG_CAM_SMEM
+                                const int4 o = lds128(cam);
+#else
+                                const int4 o = nd;
+#endif
+                                pend[cnt * 32 + lane] = sample_key(rx, ry, rz, o);
                                 ++cnt;
                             }
                         }
@@ -586,17 +546,14 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
                 if (code == kUnknown) {
                     if constexpr (STATS) ++st_unk;
                     // owner test: centre of this voxel projects into pixel (ti, tj)
+                    const int rx = voxel_offset(r.nx, r.sx);
+                    const int ry = voxel_offset(r.ny, r.sy);
+                    const int rz = voxel_offset(r.nz, r.sz);
 #if MIG_CAM_SMEM
                     const int4 c0 = lds128(cam), c1 = lds128(cam + 1);
-                    const int rx = (r.vx << 16) + 32768 - c0.x;
-                    const int ry = (r.vy << 16) + 32768 - c0.y;
-                    const int rz = (r.vz << 16) + 32768 - c0.z;
                     const int64_t Z = (int64_t)c0.w * rx + (int64_t)c1.x * ry + (int64_t)c1.y * rz;
                     const int64_t U = (int64_t)c1.z * rx + (int64_t)c1.w * ry + (int64_t)lds128(cam + 2).x * rz;
 #else
-                    const int rx = (r.vx << 16) + 32768 - nd.x;
-                    const int ry = (r.vy << 16) + 32768 - nd.y;
-                    const int rz = (r.vz << 16) + 32768 - nd.z;
                     const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * rz;
                     const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * rz;
 #endif
@@ -610,8 +567,11 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
 #endif
                         const int64_t jZ = (int64_t)tj * Z;
                         owned = V >= jZ && V < jZ + Z;
-                        samp = (unsigned long long)(uint32_t)r.vx | ((unsigned long long)(uint32_t)r.vy << 16) |
-                               ((unsigned long long)(uint32_t)r.vz << 32);
+#if MIG_CAM_SMEM
+                        samp = sample_key(rx, ry, rz, lds128(cam));
+#else
+                        samp = sample_key(rx, ry, rz, nd);
+#endif
                     }
                 }
                 have = ray_step<false>(r, ne, ade);

@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "libmig_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE = 0, 1, 2
+MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL = 0, 1, 2, 3
 
 
 _MUTANT = 0  # planted-mistake variant (pin-strength tests only); 0 = the oracle
@@ -71,12 +71,16 @@ def lib():
             L.oracle_eval_tree.argtypes = [p, i, i, i, f, p, i, p, p, f, f, i, i, f, i, f, i, p, p, p, p, p, p, p, i]
             L.oracle_camera_tables.argtypes = [f, f, i, i, i, f, p, p, p, p, p, p]
             L.oracle_ray_dirs.argtypes = [f, f, i, i, i, f, p]
-            L.oracle_trace.argtypes = [p, i, i, i, p, p, C.c_int64, C.c_int64, i, p, p, p, p]
+            L.oracle_trace.argtypes = [p, i, i, i, p, p, C.c_int64, C.c_int64, i, p, p, p, p, p]
             L.oracle_project.argtypes = [f, f, i, i, i, f, i, p, i, p, p]
             L.oracle_quantize.argtypes = [p, i, p, f, i, i, i, p]
             L.oracle_observed.argtypes = [f, f, i, i, i, f, i, p, p, p]
             L.oracle_visible_sets.argtypes = [p, i, i, i, f, p, i, p, p, f, f, i, i, f, i, f, p, p, p, i]
             L.oracle_exact_dfs.argtypes = [i, p, p, p, C.c_int64, p, p]
+            L.oracle_ray_intervals.argtypes = [f, f, i, i, i, f, i, p, p, p, p, C.c_int64, i, p, p, i, p, p, p, p]
+            i64 = C.c_int64
+            L.oracle_sample_lambda.argtypes = [i64, i64, i64, i64, i64]
+            L.oracle_sample_lambda.restype = C.c_float
             _lib = L
     return _lib
 
@@ -154,8 +158,9 @@ def ray_dirs(sensor):
     return out
 
 
-def trace(grid, P, d, Tq, dzc, cap=100000):
-    """One DDA ray; returns (voxels [m,3], codes [m], hit, D)."""
+def trace(grid, P, d, Tq, dzc, cap=100000, want_lambda=False):
+    """One DDA ray; returns (voxels [m,3], codes [m], hit, D), plus the interval-mode sample
+    fraction of each visited voxel when want_lambda."""
     grid = _c(grid, np.uint8)
     nz, ny, nx = grid.shape
     P = _c(P, np.int64)
@@ -164,13 +169,15 @@ def trace(grid, P, d, Tq, dzc, cap=100000):
     codes = np.zeros(cap, np.uint8)
     hit = np.zeros(1, np.int32)
     D = np.zeros(1, np.uint32)
+    lam = np.zeros(cap, np.float32) if want_lambda else None
     m = lib().oracle_trace(_ptr(grid), nx, ny, nz, _ptr(P), _ptr(d), int(Tq), int(dzc), cap, _ptr(vox), _ptr(codes),
-                           _ptr(hit), _ptr(D))
+                           _ptr(hit), _ptr(D), _ptr(lam))
     if m < 0:
         raise OracleError("oracle_trace: invalid ray")
     if m > cap:
         raise OracleError("oracle_trace: cap exceeded")
-    return vox[:m].copy(), codes[:m].copy(), bool(hit[0]), int(D[0])
+    out = (vox[:m].copy(), codes[:m].copy(), bool(hit[0]), int(D[0]))
+    return out + (lam[:m].copy(),) if want_lambda else out
 
 
 def project(sensor, k, P, vox):
@@ -194,6 +201,37 @@ def observed(sensor, k, P, D, vox):
     if rc < 0:
         raise OracleError("oracle_observed failed")
     return bool(rc)
+
+
+def ray_intervals(sensor, ka, Pa, D, P, d, Tq, lam=()):
+    """The interval construction (Sec. IV-B, Eq. 5-7) of one candidate ray (origin P, Q16; direction
+    d, Q30; range Tq, Q16) against one ancestor (position Pa, yaw bin ka, depth buffer D [H, W]).
+
+    Returns a dict: seg (lo, hi, Za, Zb, ua, va, ub, vb, wa, wb, s0, s1), portions [m, 3]
+    (s_in, s_out, observed) and their pixels [m, 2] in walk order, and for each ray fraction in
+    `lam` its screen parameter and observation (-1 = outside the ancestor's depth range or image)."""
+    W, H = sensor.width, sensor.height
+    cap = W + H + 2
+    lam = _c(np.asarray(lam, np.float32).reshape(-1), np.float32)
+    seg = np.zeros(12, np.float32)
+    por = np.zeros((cap, 3), np.float32)
+    pix = np.zeros((cap, 2), np.int32)
+    lo = np.zeros(max(1, lam.size), np.int32)
+    ls = np.zeros(max(1, lam.size), np.float32)
+    m = lib().oracle_ray_intervals(float(sensor.hfov_deg), float(sensor.vfov_deg), W, H, sensor.yaw_bins,
+                                   float(sensor.pitch_deg), int(ka), _ptr(_c(Pa, np.int64)), _ptr(_c(D, np.uint32)),
+                                   _ptr(_c(P, np.int64)), _ptr(_c(d, np.int64)), int(Tq), int(lam.size), _ptr(lam),
+                                   _ptr(seg), cap, _ptr(por), _ptr(pix), _ptr(lo), _ptr(ls))
+    if m < 0:
+        raise OracleError("oracle_ray_intervals failed")
+    return {"seg": seg, "portions": por[:m].copy(), "pixels": pix[:m].copy(), "lam_obs": lo[:lam.size].copy(),
+            "lam_s": ls[:lam.size].copy()}
+
+
+def sample_lambda(ne, ade, nx, adx, Tq):
+    """Interval mode: a voxel's sample, the midpoint of the ray's traversal (entry ne/ade, exit
+    nx/adx, capped at the range), as a fraction of the range."""
+    return float(lib().oracle_sample_lambda(int(ne), int(ade), int(nx), int(adx), int(Tq)))
 
 
 def quantize(pos, origin, voxel, dims):

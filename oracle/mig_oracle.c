@@ -33,7 +33,7 @@ typedef int64_t i64;
 #define OR_OCCUPIED 2
 #define OR_MAX_DEPTH 64
 
-enum { MODE_MARGINAL = 0, MODE_SINGLE_PARENT = 1, MODE_ABSOLUTE = 2 };
+enum { MODE_MARGINAL = 0, MODE_SINGLE_PARENT = 1, MODE_ABSOLUTE = 2, MODE_INTERVAL = 3 };
 
 /* Planted mistakes for the pin-strength tests (tests/test_oracle_mutants.py). The default
  * build defines none; each variant .so is built with -DORACLE_MUTANT=<m> and must fail at
@@ -169,7 +169,9 @@ static uint8_t grid_at(const grid_t *G, const int32_t v[3]) {
  * hit's entry point in Q16 voxel units through *D (Sec. IV-A), else 0 and the range
  * endpoint's depth.
  * ------------------------------------------------------------------------------------ */
-typedef int (*visit_fn)(void *ctx, const int32_t v[3], uint8_t code);
+/* The visitor also receives the voxel's entry crossing te = (n, |d|) (t = n / |d|; (0, 1) for the
+ * start voxel) and its exit crossing tx (the next crossing in the traversal order). */
+typedef int (*visit_fn)(void *ctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]);
 
 static int dda(const grid_t *G, const i64 P[3], const i64 d[3], i64 Tq, i64 dzc, visit_fn fn, void *ctx,
                uint32_t *D) {
@@ -185,15 +187,18 @@ static int dda(const grid_t *G, const i64 P[3], const i64 d[3], i64 Tq, i64 dzc,
     i64 ne = 0, ade = 1; /* entry t of the current voxel = ne / ade (scaled) */
     for (;;) {
         uint8_t code = grid_at(G, v);
-        if (fn) fn(ctx, v, code);
-        if (code == OR_OCCUPIED) {
-            if (D) *D = (uint32_t)floor_div((MUT(7) && ade > 1 ? ne + ONE_Q16 : ne) * dzc, ade);
-            return 1;
-        }
         int best = -1;
         for (int a = 0; a < 3; ++a) {
             if (ad[a] == 0) continue;
             if (best < 0 || (MUT(5) ? nn[a] * ad[best] <= nn[best] * ad[a] : nn[a] * ad[best] < nn[best] * ad[a])) best = a;
+        }
+        if (fn) {
+            const i64 te[2] = {ne, ade}, tx[2] = {nn[best], ad[best]};
+            fn(ctx, v, code, te, tx);
+        }
+        if (code == OR_OCCUPIED) {
+            if (D) *D = (uint32_t)floor_div((MUT(7) && ade > 1 ? ne + ONE_Q16 : ne) * dzc, ade);
+            return 1;
         }
         /* next entry t = nn[best]/ad[best] (voxel units: nn * 2^14 / ad); stop if >= T */
         if (MUT(6) ? nn[best] * ONE_Q30 > Tq * ad[best] : nn[best] * ONE_Q30 >= Tq * ad[best]) break;
@@ -240,13 +245,212 @@ static int observed_by(const cam_t *c, const i64 Pa[3], int ka, const uint32_t *
     return MUT(10) ? Z < Dq * ONE_Q16 : Z < (Dq + 1) * ONE_Q16; /* floor(z in Q16) <= stored depth */
 }
 
-static int count_visit(void *vctx, const int32_t v[3], uint8_t code) {
+static int count_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]) {
+    (void)te;
+    (void)tx;
     count_ctx *x = (count_ctx *)vctx;
     if (code != OR_UNKNOWN) return 0;
     if (!MUT(8) && !owned(x->cam, x->k, x->P, v, x->pi, x->pj)) return 0;
     x->abs_count++;
     for (int a = 0; a < x->n_anc; ++a)
         if (observed_by(x->cam, x->anc_P[a], x->anc_yaw[a], x->anc_D[a], v)) return 0;
+    x->marg_count++;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Interval mode: the screen-space overlap of Sec. IV-B (Eq. 5-7), restated in the paper's
+ * order. For a candidate ray r(t) = p_n + t d (0 <= t <= range) and each ancestor a:
+ *   1. the ray's start and range endpoint in a's camera, as projective image coordinates
+ *      (U, V, Z) = M_a (x - p_a) (exact integers, Q32, then IEEE float in voxel units);
+ *      (U, V, Z) is linear in the ray fraction lambda = t / range;
+ *   2. clip along camera z to the valid depth range [Z_NEAR, range] (Sec. IV-B: the
+ *      "valid depth range"; depths beyond the range can never be <= a stored depth);
+ *   3. project the clipped endpoints (Eq. 5), u = U / Z, v = V / Z, with inverse depths
+ *      w = 1 / Z, and clip the 2D segment to the buffer [0, W] x [0, H] (Liang-Barsky);
+ *   4. walk the pixels of the clipped segment with a 2D DDA ("Woo 1987"). Each visited pixel
+ *      holds one portion [s_in, s_out) of the segment parameter s; its depth sample is taken
+ *      at the portion's midpoint with w linear in s (Eq. 6), z = 1 / w, and the portion is
+ *      observed iff z <= D_a[pixel] ("smaller or equal"). The maximal runs of observed
+ *      portions are the intervals S_a of Eq. 7.
+ * Then the 3D DDA counts (Sec. IV-B, last paragraph): an owned unknown voxel is a sample at
+ * the midpoint of the ray's traversal of it (lambda_s, the exit capped at the range); it is
+ * observed iff it lies in the union of the S_a, i.e. iff for some ancestor its screen
+ * parameter s (perspective-correct, from lambda_s) falls in an observed portion. Each sample
+ * is classified by the first portion in walk order with s_in <= s < s_out.
+ * All steps after the exact projective endpoints are IEEE single-precision operations in a
+ * fixed order (no contraction): the decisions are reproducible bit for bit.
+ * ------------------------------------------------------------------------------------ */
+#define Z_NEAR (1.0f / 1024.0f) /* voxel units */
+
+typedef struct {
+    float lo, hi;         /* depth-clipped range of lambda */
+    float Za, Zb;         /* camera z at lo, hi (voxel units) */
+    float ua, va, ub, vb; /* projected clipped endpoints (pixels) */
+    float wa, wb;         /* inverse depths at the endpoints */
+    float s0, s1;         /* Liang-Barsky range of s over [0, 1] */
+} seg2d_t;
+
+typedef struct {
+    float s_in, s_out;
+    int obs;
+    int i, j; /* the pixel */
+} portion_t;
+
+/* range endpoint of the ray, Q16: E = P + floor(T d / 2^30) */
+static void ray_end(const i64 P[3], const i64 d[3], i64 Tq, i64 E[3]) {
+    for (int a = 0; a < 3; ++a) E[a] = P[a] + floor_div(Tq * d[a], ONE_Q30);
+}
+
+/* steps 1-3; returns 0 if nothing of the ray is inside a's depth range and image */
+static int seg_setup(const cam_t *c, int ka, const i64 Pa[3], const i64 P[3], const i64 E[3], i64 Tq, seg2d_t *g) {
+    const int32_t *m = c->M + (size_t)ka * 9;
+    i64 r0[3], r1[3];
+    for (int a = 0; a < 3; ++a) { r0[a] = P[a] - Pa[a]; r1[a] = E[a] - Pa[a]; }
+    const float sc = 1.0f / 4294967296.0f; /* Q32 -> voxel units (exact power of two) */
+    float U0 = (float)(m[0] * r0[0] + m[1] * r0[1] + m[2] * r0[2]) * sc;
+    float V0 = (float)(m[3] * r0[0] + m[4] * r0[1] + m[5] * r0[2]) * sc;
+    float Z0 = (float)(m[6] * r0[0] + m[7] * r0[1] + m[8] * r0[2]) * sc;
+    float U1 = (float)(m[0] * r1[0] + m[1] * r1[1] + m[2] * r1[2]) * sc;
+    float V1 = (float)(m[3] * r1[0] + m[4] * r1[1] + m[5] * r1[2]) * sc;
+    float Z1 = (float)(m[6] * r1[0] + m[7] * r1[1] + m[8] * r1[2]) * sc;
+    const float zn = Z_NEAR, zf = (float)Tq * (1.0f / 65536.0f);
+    float dZ = Z1 - Z0, lo = 0.0f, hi = 1.0f;
+    if (Z0 < zn) { if (!(dZ > 0.0f)) return 0; lo = (zn - Z0) / dZ; }
+    if (Z1 < zn) { if (!(dZ < 0.0f)) return 0; hi = (zn - Z0) / dZ; }
+    if (Z0 > zf) { if (!(dZ < 0.0f)) return 0; float l = (zf - Z0) / dZ; if (l > lo) lo = l; }
+    if (Z1 > zf) { if (!(dZ > 0.0f)) return 0; float h = (zf - Z0) / dZ; if (h < hi) hi = h; }
+    if (!(lo < hi)) return 0;
+    float dU = U1 - U0, dV = V1 - V0;
+    float Ua = U0 + lo * dU, Va = V0 + lo * dV, Za = Z0 + lo * dZ;
+    float Ub = U0 + hi * dU, Vb = V0 + hi * dV, Zb = Z0 + hi * dZ;
+    if (!(Za > 0.0f && Zb > 0.0f)) return 0;
+    g->lo = lo; g->hi = hi; g->Za = Za; g->Zb = Zb;
+    g->ua = Ua / Za; g->va = Va / Za; g->ub = Ub / Zb; g->vb = Vb / Zb;
+    g->wa = 1.0f / Za; g->wb = 1.0f / Zb;
+    /* Liang-Barsky ("Liang 1984") against 0 <= u <= W, 0 <= v <= H */
+    float du = g->ub - g->ua, dv = g->vb - g->va;
+    float p[4] = {-du, du, -dv, dv};
+    float q[4] = {g->ua, (float)c->W - g->ua, g->va, (float)c->H - g->va};
+    float s0 = 0.0f, s1 = 1.0f;
+    for (int e = 0; e < 4; ++e) {
+        if (p[e] == 0.0f) { if (q[e] < 0.0f) return 0; continue; }
+        float r = q[e] / p[e];
+        if (p[e] < 0.0f) { if (r > s1) return 0; if (r > s0) s0 = r; }
+        else { if (r < s0) return 0; if (r < s1) s1 = r; }
+    }
+    if (!(s0 < s1)) return 0;
+    g->s0 = s0; g->s1 = s1;
+    return 1;
+}
+
+/* step 4: the 2D DDA over the clipped segment; writes the portions in walk order */
+static int seg_walk(const seg2d_t *g, int W, int H, const uint32_t *D, portion_t *out) {
+    float du = g->ub - g->ua, dv = g->vb - g->va;
+    float s = g->s0;
+    int i = (int)floorf(g->ua + s * du), j = (int)floorf(g->va + s * dv);
+    if (i < 0) i = 0;
+    if (i > W - 1) i = W - 1;
+    if (j < 0) j = 0;
+    if (j > H - 1) j = H - 1;
+    int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
+    float sx = si ? ((float)(si > 0 ? i + 1 : i) - g->ua) / du : INFINITY;
+    float sy = sj ? ((float)(sj > 0 ? j + 1 : j) - g->va) / dv : INFINITY;
+    int np = 0;
+    for (;;) {
+        float se = sx < sy ? sx : sy;
+        if (g->s1 < se) se = g->s1;
+        float sm = MUT(14) ? s : (s + se) * 0.5f;  /* Eq. 6 at the portion's midpoint */
+        float wm = g->wa + sm * (g->wb - g->wa);
+        float zm = 1.0f / wm;
+        float Dv = (float)D[(size_t)j * W + i] * (1.0f / 65536.0f);
+        out[np].s_in = s;
+        out[np].s_out = se;
+        out[np].obs = MUT(16) ? zm < Dv : zm <= Dv;
+        out[np].i = i;
+        out[np].j = j;
+        np++;
+        if (!(se < g->s1)) break;
+        if (sx <= sy) {
+            i += si;
+            if (i < 0 || i >= W) break;
+            sx = ((float)(si > 0 ? i + 1 : i) - g->ua) / du;
+        } else {
+            j += sj;
+            if (j < 0 || j >= H) break;
+            sy = ((float)(sj > 0 ? j + 1 : j) - g->va) / dv;
+        }
+        s = se;
+    }
+    return np;
+}
+
+/* screen parameter of the ray fraction lam (perspective-correct); 0 if outside the clip */
+static int seg_param(const seg2d_t *g, float lam, float *s) {
+    if (!(lam >= g->lo && lam <= g->hi)) return 0;
+    float mu = (lam - g->lo) / (g->hi - g->lo);
+    float num = mu * g->Zb;
+    float den = (1.0f - mu) * g->Za + num;
+    *s = MUT(15) ? mu : num / den;
+    return *s >= g->s0 && *s < g->s1;
+}
+
+/* observed by one ancestor: the first portion (walk order) that contains s decides */
+static int portions_observe(const portion_t *pt, int np, float s) {
+    for (int q = 0; q < np; ++q)
+        if (pt[q].s_in <= s && s < pt[q].s_out) return pt[q].obs;
+    return 0;
+}
+
+/* the voxel's sample: midpoint of the ray's traversal of it, as a fraction of the range */
+static float sample_lambda(const i64 te[2], const i64 tx[2], i64 Tq) {
+    const float T = (float)Tq * (1.0f / 1073741824.0f);
+    float lin = ((float)te[0] / (float)te[1]) / T;
+    float lout = ((float)tx[0] / (float)tx[1]) / T;
+    if (lout > 1.0f) lout = 1.0f;
+    return MUT(17) ? lin : (lin + lout) * 0.5f;
+}
+
+typedef struct {
+    const cam_t *cam;
+    int k;
+    i64 pi, pj;
+    const i64 *P;
+    i64 E[3]; /* the ray's range endpoint */
+    i64 Tq;
+    int n_anc;
+    const i64 (*anc_P)[3];
+    const int *anc_yaw;
+    uint32_t *const *anc_D;
+    int built;            /* the S_a of this ray are built (on its first sample) */
+    seg2d_t *seg;         /* per ancestor */
+    int *seg_ok, *n_por;  /* per ancestor */
+    portion_t *por;       /* per ancestor, W + H + 2 each */
+    i64 abs_count, marg_count;
+} ival_ctx;
+
+static void build_intervals(ival_ctx *x) {
+    const int cap = x->cam->W + x->cam->H + 2;
+    for (int a = 0; a < x->n_anc; ++a) {
+        x->seg_ok[a] = seg_setup(x->cam, x->anc_yaw[a], x->anc_P[a], x->P, x->E, x->Tq, &x->seg[a]);
+        x->n_por[a] = x->seg_ok[a] ? seg_walk(&x->seg[a], x->cam->W, x->cam->H, x->anc_D[a], x->por + (size_t)a * cap) : 0;
+    }
+    x->built = 1;
+}
+
+static int interval_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]) {
+    ival_ctx *x = (ival_ctx *)vctx;
+    if (code != OR_UNKNOWN) return 0;
+    if (!owned(x->cam, x->k, x->P, v, x->pi, x->pj)) return 0;
+    x->abs_count++;
+    if (!x->built) build_intervals(x);
+    const int cap = x->cam->W + x->cam->H + 2;
+    float lam = sample_lambda(te, tx, x->Tq);
+    for (int a = 0; a < x->n_anc; ++a) {
+        float sp;
+        if (!x->seg_ok[a] || !seg_param(&x->seg[a], lam, &sp)) continue;
+        if (portions_observe(x->por + (size_t)a * cap, x->n_por[a], sp)) return 0;
+    }
     x->marg_count++;
     return 0;
 }
@@ -289,7 +493,7 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
                      int32_t *cnt_abs, int32_t *cnt_marg, uint32_t *depth_out, int n_threads) {
     if (n < 0 || nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return -1;
     if (!(voxel > 0.0f)) return -1;
-    if (mode < 0 || mode > 2) return -1;
+    if (mode < 0 || mode > 3) return -1;
     if (n == 0) return 0;
     for (size_t i = 0, m = (size_t)nx * ny * nz; i < m; ++i)
         if (grid[i] > OR_OCCUPIED) return -1;
@@ -343,6 +547,38 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
                         na++;
                         if (mode == MODE_SINGLE_PARENT || MUT(9)) break;
                     }
+                }
+                if (mode == MODE_INTERVAL) {
+                    /* Sec. IV-B: per ray, the ancestors' overlap intervals, then the 3D DDA */
+                    const size_t cap = (size_t)W + H + 2;
+                    ival_ctx y;
+                    memset(&y, 0, sizeof(y));
+                    y.cam = &cam; y.k = k; y.P = P[nd]; y.Tq = Tq; y.n_anc = na;
+                    y.anc_P = (const i64(*)[3])anc_P; y.anc_yaw = anc_yaw; y.anc_D = anc_D;
+                    y.seg = malloc((size_t)(na > 0 ? na : 1) * sizeof(seg2d_t));
+                    y.seg_ok = malloc((size_t)(na > 0 ? na : 1) * sizeof(int));
+                    y.n_por = malloc((size_t)(na > 0 ? na : 1) * sizeof(int));
+                    y.por = malloc((size_t)(na > 0 ? na : 1) * cap * sizeof(portion_t));
+                    if (!y.seg || !y.seg_ok || !y.n_por || !y.por) {
+                        rc = -2;
+                    } else {
+                        for (int j = 0; j < H; ++j) {
+                            for (int i = 0; i < W; ++i) {
+                                size_t p = (size_t)j * W + i;
+                                i64 dvec[3];
+                                cam_dir(&cam, k, p, dvec);
+                                y.pi = i;
+                                y.pj = j;
+                                y.built = 0;
+                                ray_end(P[nd], dvec, Tq, y.E);
+                                dda(&G, P[nd], dvec, Tq, cam.dzc[p], interval_visit, &y, NULL);
+                            }
+                        }
+                    }
+                    free(y.seg); free(y.seg_ok); free(y.n_por); free(y.por);
+                    cabs[(size_t)nd * K + k] = (int32_t)y.abs_count;
+                    cmarg[(size_t)nd * K + k] = (int32_t)y.marg_count;
+                    continue;
                 }
                 count_ctx x = {&cam, &G, k, 0, 0, P[nd], na, (const i64(*)[3])anc_P, anc_yaw, anc_D, 0, 0};
                 for (int j = 0; j < H; ++j) {
@@ -447,14 +683,17 @@ int oracle_ray_dirs(float hfov, float vfov, int W, int H, int K, float pitch, in
 typedef struct {
     int32_t *out;
     uint8_t *codes;
+    float *lam; /* interval-mode sample of each visited voxel (optional) */
+    i64 Tq;
     int cap, count;
 } trace_ctx;
 
-static int trace_visit(void *vctx, const int32_t v[3], uint8_t code) {
+static int trace_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]) {
     trace_ctx *t = (trace_ctx *)vctx;
     if (t->count < t->cap) {
         t->out[3 * t->count] = v[0]; t->out[3 * t->count + 1] = v[1]; t->out[3 * t->count + 2] = v[2];
         if (t->codes) t->codes[t->count] = code;
+        if (t->lam) t->lam[t->count] = sample_lambda(te, tx, t->Tq);
     }
     t->count++;
     return 0;
@@ -463,12 +702,12 @@ static int trace_visit(void *vctx, const int32_t v[3], uint8_t code) {
 /* One ray: P (Q16), d (Q30), T (Q16), dzc (Q30). Writes up to cap visited voxels; returns
  * the number visited (may exceed cap), *hit, *D. */
 int oracle_trace(const uint8_t *grid, int nx, int ny, int nz, const int64_t *P, const int64_t *d, int64_t Tq,
-                 int64_t dzc, int cap, int32_t *vox, uint8_t *codes, int32_t *hit, uint32_t *D) {
+                 int64_t dzc, int cap, int32_t *vox, uint8_t *codes, int32_t *hit, uint32_t *D, float *lam) {
     grid_t G = {grid, {nx, ny, nz}};
     for (int a = 0; a < 3; ++a)
         if (P[a] < 0 || P[a] >= (i64)G.n[a] * ONE_Q16) return -1;
     if (d[0] == 0 && d[1] == 0 && d[2] == 0) return -1;
-    trace_ctx t = {vox, codes, cap, 0};
+    trace_ctx t = {vox, codes, lam, Tq, cap, 0};
     uint32_t Dv = 0;
     *hit = dda(&G, P, d, Tq, dzc, trace_visit, &t, &Dv);
     *D = Dv;
@@ -501,6 +740,51 @@ int oracle_observed(float hfov, float vfov, int W, int H, int K, float pitch, in
     return r;
 }
 
+/* The interval construction of one candidate ray against one ancestor (for pins):
+ * seg_out[12] = lo, hi, Za, Zb, ua, va, ub, vb, wa, wb, s0, s1; portions (s_in, s_out, obs,
+ * pixel i, j) in walk order; for each ray fraction lam[q]: its screen parameter and whether
+ * the ancestor observes it (-1: outside the depth range or image). Returns the number of
+ * portions (0 = nothing of the ray in the ancestor's view), or < 0 on bad input. */
+int oracle_ray_intervals(float hfov, float vfov, int W, int H, int K, float pitch, int ka, const int64_t *Pa,
+                         const uint32_t *D, const int64_t *P, const int64_t *d, int64_t Tq, int n_lam,
+                         const float *lam, float *seg_out, int cap, float *por_out, int32_t *por_pix,
+                         int32_t *lam_obs, float *lam_s) {
+    cam_t c;
+    int rc = cam_build(&c, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    if (ka < 0 || ka >= K || cap < W + H + 2) { cam_free(&c); return -1; }
+    i64 E[3];
+    ray_end(P, d, Tq, E);
+    seg2d_t g;
+    memset(&g, 0, sizeof(g));
+    int ok = seg_setup(&c, ka, Pa, P, E, Tq, &g);
+    float gv[12] = {g.lo, g.hi, g.Za, g.Zb, g.ua, g.va, g.ub, g.vb, g.wa, g.wb, g.s0, g.s1};
+    memcpy(seg_out, gv, sizeof(gv));
+    int np = 0;
+    portion_t *pt = malloc((size_t)cap * sizeof(portion_t));
+    if (!pt) { cam_free(&c); return -2; }
+    if (ok) np = seg_walk(&g, W, H, D, pt);
+    for (int q = 0; q < np; ++q) {
+        por_out[3 * q] = pt[q].s_in; por_out[3 * q + 1] = pt[q].s_out; por_out[3 * q + 2] = (float)pt[q].obs;
+        por_pix[2 * q] = pt[q].i; por_pix[2 * q + 1] = pt[q].j;
+    }
+    for (int q = 0; q < n_lam; ++q) {
+        float sp = 0.0f;
+        int in = ok && seg_param(&g, lam[q], &sp);
+        lam_s[q] = sp;
+        lam_obs[q] = in ? portions_observe(pt, np, sp) : -1;
+    }
+    free(pt);
+    cam_free(&c);
+    return np;
+}
+
+/* the interval mode's sample of a voxel: traversal midpoint as a fraction of the range */
+float oracle_sample_lambda(int64_t ne, int64_t ade, int64_t nx, int64_t adx, int64_t Tq) {
+    const i64 te[2] = {ne, ade}, tx[2] = {nx, adx};
+    return sample_lambda(te, tx, Tq);
+}
+
 int oracle_quantize(const float *pos, int n, const float *origin, float voxel, int nx, int ny, int nz, int64_t *P) {
     int dims[3] = {nx, ny, nz};
     for (int i = 0; i < n; ++i)
@@ -521,7 +805,9 @@ typedef struct {
     i64 count, cap;
 } set_ctx;
 
-static int set_visit(void *vctx, const int32_t v[3], uint8_t code) {
+static int set_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]) {
+    (void)te;
+    (void)tx;
     set_ctx *s = (set_ctx *)vctx;
     if (code != OR_UNKNOWN) return 0;
     if (!owned(s->cam, s->k, s->P, v, s->pi, s->pj)) return 0;

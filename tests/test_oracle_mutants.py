@@ -3,15 +3,18 @@
 The mistakes are the plausible ones: a dropped pixel-centre offset, a mirrored axis,
 truncation instead of floor, a dropped projection term, a reversed DDA tie rule, an
 inclusive range test, exit instead of entry depth, no owner test, parent-only exclusion,
-a strict depth comparison, highest-index yaw ties, a flipped yaw sign, and an exact route
-that double counts."""
+a strict depth comparison, highest-index yaw ties, a flipped yaw sign, an exact route
+that double counts, and in the interval mode (Eq. 5-7): a depth sample at the portion's
+entry instead of its midpoint, a screen parameter without perspective correction, a strict
+depth comparison, and a voxel sample at the voxel's entry instead of its traversal midpoint."""
 import pytest
 
 import oracle
+import test_oracle_interval as ipins  # noqa: E402
 import test_oracle_pins as pins  # noqa: E402
 from synth import Sensor
 
-MUTANTS = list(range(1, 14))
+MUTANTS = list(range(1, 18))
 
 PIN_CALLS = [
     lambda o: pins.test_dda_matches_exact_slab_brute_force(o),
@@ -29,6 +32,15 @@ PIN_CALLS = [
     lambda o: pins.test_disjoint_frusta_and_identical_pose(o),
     lambda o: pins.test_exact_routes_agree_and_telescope(o, 2),
     lambda o: pins.test_tiny_config_gap_is_small_and_positive(o),
+    lambda o: ipins.test_interval_segment_matches_float_camera(o, ipins.SENSORS[1]),
+    lambda o: ipins.test_interval_walk_tiles_the_clipped_segment(o, ipins.SENSORS[1]),
+    lambda o: ipins.test_interval_depth_sample_is_perspective_midpoint_smaller_or_equal(o, ipins.SENSORS[0]),
+    lambda o: ipins.test_interval_equal_depth_counts_as_observed(o),
+    lambda o: ipins.test_interval_sample_parameter_is_perspective_correct(o, ipins.SENSORS[0]),
+    lambda o: ipins.test_interval_voxel_sample_is_traversal_midpoint(o),
+    lambda o: ipins.test_interval_mode_invariants(o, 1),
+    lambda o: ipins.test_interval_mode_special_cases(o),
+    lambda o: ipins.test_interval_mode_gap_to_exact_tiny(o),
 ]
 
 

@@ -75,8 +75,20 @@ typedef struct mig_sensor {
 } mig_sensor;
 
 /* Gain formulation (Sec. III-B, Sec. V-A): marginal over all ancestors (Eq. 2, the default),
- * single-parent exclusion g_sp, or absolute gain (Eq. 1, no exclusion; yaw = argmax abs). */
-typedef enum { MIG_MODE_MARGINAL = 0, MIG_MODE_SINGLE_PARENT = 1, MIG_MODE_ABSOLUTE = 2 } mig_mode;
+ * single-parent exclusion g_sp, or absolute gain (Eq. 1, no exclusion; yaw = argmax abs).
+ * MIG_MODE_INTERVAL is the marginal gain with the paper's screen-space overlap test (Sec. IV-B,
+ * Eq. 5-7) in place of the voxel-centre test: per ancestor, the candidate ray is clipped to the
+ * valid depth range, projected, clipped to the buffer (Liang-Barsky) and walked pixel by pixel
+ * (2D DDA), one inverse-depth sample per visited pixel (Eq. 6); an owned unknown voxel, sampled
+ * at the midpoint of the ray's traversal of it, is excluded when it falls in an observed
+ * portion of any ancestor. Accepted by mig_tree_eval_ex (and mig_tree_eval_stats) only; the
+ * batched, served and device-resident entry points return MIG_EINVAL for it. */
+typedef enum {
+    MIG_MODE_MARGINAL = 0,
+    MIG_MODE_SINGLE_PARENT = 1,
+    MIG_MODE_ABSOLUTE = 2,
+    MIG_MODE_INTERVAL = 3
+} mig_mode;
 
 /* ---------------------------------------------------------------------------------------
  * Context: one GPU, one CUDA stream, one allocator. `stream` is a cudaStream_t (NULL = the

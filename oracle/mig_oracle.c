@@ -348,11 +348,10 @@ static int seg_setup(const cam_t *c, int ka, const i64 Pa[3], const i64 P[3], co
 static int seg_walk(const seg2d_t *g, int W, int H, const uint32_t *D, portion_t *out) {
     float du = g->ub - g->ua, dv = g->vb - g->va;
     float s = g->s0;
-    int i = (int)floorf(g->ua + s * du), j = (int)floorf(g->va + s * dv);
-    if (i < 0) i = 0;
-    if (i > W - 1) i = W - 1;
-    if (j < 0) j = 0;
-    if (j > H - 1) j = H - 1;
+    /* start pixel, clamped to the buffer in float (before any conversion to int) */
+    float fi = floorf(g->ua + s * du), fj = floorf(g->va + s * dv);
+    int i = fi < 0.0f ? 0 : (fi > (float)(W - 1) ? W - 1 : (int)fi);
+    int j = fj < 0.0f ? 0 : (fj > (float)(H - 1) ? H - 1 : (int)fj);
     int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
     float sx = si ? ((float)(si > 0 ? i + 1 : i) - g->ua) / du : INFINITY;
     float sy = sj ? ((float)(sj > 0 ? j + 1 : j) - g->va) / dv : INFINITY;

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "interval.h"
 #include "kernels.h"
 #include "mig_impl.h"
 
@@ -211,6 +212,7 @@ mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocat
     }
     MIG_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     ctx->count_ctas = count_ctas_per_sm();
+    ctx->interval_ctas = count_interval_ctas_per_sm();
     ctx->d_err = (int32_t *)ctx->alloc.alloc(256, ctx->stream);
     if (!ctx->d_err) return fail(MIG_ENOMEM, "ctx_create: allocation failed");
     MIG_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream));
@@ -423,7 +425,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     if (n < 0) return fail(MIG_EINVAL, "tree_eval: negative node count");
     if (n > 0 && (!abs_gain || !marg_gain || !best_yaw)) return fail(MIG_EINVAL, "tree_eval: output array is NULL");
     const int mode = opts ? opts->mode : MIG_MODE_MARGINAL;
-    if (mode < 0 || mode > 2) return fail(MIG_EINVAL, "tree_eval: unknown mode");
+    if (mode < 0 || mode > MIG_MODE_INTERVAL) return fail(MIG_EINVAL, "tree_eval: unknown mode");
     mig_status st = sensor_check(*sensor, m->voxel);
     if (st != MIG_OK) return st;
     if (n == 0) return MIG_OK;
@@ -502,7 +504,13 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         const int Ld = plan.level_off[d + 1] - plan.level_off[d];
         const int items = Ld * K * p.tiles;
         const int cgrid = std::max(1, std::min((items + 7) / 8, count_cap));
-        timed_launch(ctx, kProfCount, [&] { launch_count(p, cgrid, ctx->stream); });
+        if (mode == MIG_MODE_INTERVAL)
+            timed_launch(ctx, kProfCount, [&] {
+                launch_count_interval(p, std::max(1, std::min((items + 7) / 8, ctx->num_sms * ctx->interval_ctas)),
+                                      ctx->stream);
+            });
+        else
+            timed_launch(ctx, kProfCount, [&] { launch_count(p, cgrid, ctx->stream); });
         timed_launch(ctx, kProfSelect,
                      [&] { launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), ctx->stream); });
         const int ritems = plan.level_int[d] * render_tiles(p.W, p.H);

@@ -148,7 +148,8 @@ __device__ __forceinline__ void ray_dir(const int4 b, int ck, int sk, int &dx, i
 
 // One step of the DDA: picks the axis with the smallest next crossing (ties x, y, z), stops if
 // that crossing leaves the grid or starts at t >= T. Returns false when the ray ends.
-// DEPTH: also report the entry face distance / speed (ne / ade) of the new voxel.
+// DEPTH: also report that crossing's face distance / speed (ne / ade): the exit of the current
+// voxel, which is the entry of the new one when the step is taken (reported on either return).
 template <bool DEPTH>
 __device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) {
     // lexicographic minimum of (t, axis) in two comparisons: the earlier of x and y (ties x), then
@@ -159,11 +160,11 @@ __device__ __forceinline__ bool ray_step(RayIn &r, uint32_t &ne, uint32_t &ade) 
     const bool bx = !bz && xly;
     const bool by = !bz && !xly;
     const uint32_t nc = bz ? r.nz : nw;
-    if (nc >= (bz ? r.lz : lw)) return false;
     if constexpr (DEPTH) {
         ne = nc;
         ade = bz ? r.adz : aw;
     }
+    if (nc >= (bz ? r.lz : lw)) return false;
     r.nx += bx ? kQ16 : 0u;
     r.ny += by ? kQ16 : 0u;
     r.nz += bz ? kQ16 : 0u;

@@ -1,0 +1,361 @@
+// Interval-mode count pass: the paper's screen-space overlap test (Sec. IV-B, Eq. 5-7).
+//
+// For every candidate ray the 3D DDA (Sec. IV-B) visits voxels exactly as in the sample mode;
+// each owned unknown voxel (reading A1) counts as absolute gain and becomes a sample at the
+// midpoint of the ray's traversal of it. A sample is excluded from the marginal gain when it
+// lies in the union of the ancestors' overlap intervals of the ray. For each ancestor the ray is
+//   1. taken to the ancestor's camera as projective image coordinates (U, V, Z), exact integers
+//      from the Q16 projection rows, then IEEE single precision in voxel units;
+//   2. clipped to the valid depth range [Z_NEAR, range];
+//   3. projected (Eq. 5) and clipped to the buffer [0, W] x [0, H] (Liang-Barsky);
+//   4. walked pixel by pixel (2D DDA); each visited pixel holds one portion of the segment, whose
+//      depth sample at the portion's midpoint (inverse depth linear in the screen parameter,
+//      Eq. 6) is compared with the stored depth, "smaller or equal" => observed.
+// A sample belongs to the first portion, in walk order, that contains its perspective-correct
+// screen parameter. Every floating-point step is one correctly rounded single-precision
+// operation (__fadd_rn and friends: no contraction), in a fixed order, so the counts are
+// reproducible bit for bit.
+//
+// Layout: one warp per work item (node, yaw, tile of rays), taken from the level's atomic work
+// counter; each lane casts rays lane, lane + 32, ... of the tile. A lane keeps up to kIvChunk
+// pending samples (ray fractions) in shared memory and runs the ancestors' interval walks over
+// them when the buffer fills or the ray ends, so the walks are paid only by rays with samples.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dev_path.cuh"
+#include "interval.h"
+#include "kernels.h"
+#include "mig.h"
+
+namespace mig {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kIvWarps = 8;
+constexpr int kIvThreads = kIvWarps * 32;
+constexpr int kIvChunk = 16;  // pending samples per lane
+constexpr float kZNear = 1.0f / 1024.0f;  // near end of the valid depth range, voxel units
+
+// an ancestor as the interval walk needs it: position (Q16), selected yaw, depth buffer
+struct IvAnc {
+    int px, py, pz, yaw;
+    const uint32_t *D;
+};
+
+struct Seg {
+    float lo, hi;          // depth-clipped range of the ray fraction
+    float Za, Zb;          // camera z at lo, hi (voxel units)
+    float ua, va, ub, vb;  // projected clipped endpoints (pixels)
+    float wa, wb;          // inverse depths at the endpoints
+    float s0, s1;          // Liang-Barsky range of the screen parameter
+};
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// steps 1-3 for the candidate ray from P to its range endpoint E (Q16) and the ancestor at Pa
+// with projection rows m (Q16: mu, mv, mz); false if nothing of the ray is in view
+__device__ bool seg_setup(const int32_t *m, const int3 Pa, const int64_t P[3], const int64_t E[3], float zf, int W,
+                          int H, Seg &g) {
+    const int64_t r0x = P[0] - Pa.x, r0y = P[1] - Pa.y, r0z = P[2] - Pa.z;
+    const int64_t r1x = E[0] - Pa.x, r1y = E[1] - Pa.y, r1z = E[2] - Pa.z;
+    const float sc = 2.3283064365386963e-10f;  // 2^-32: Q32 -> voxel units
+    const float U0 = fmul(__ll2float_rn((int64_t)m[0] * r0x + (int64_t)m[1] * r0y + (int64_t)m[2] * r0z), sc);
+    const float V0 = fmul(__ll2float_rn((int64_t)m[3] * r0x + (int64_t)m[4] * r0y + (int64_t)m[5] * r0z), sc);
+    const float Z0 = fmul(__ll2float_rn((int64_t)m[6] * r0x + (int64_t)m[7] * r0y + (int64_t)m[8] * r0z), sc);
+    const float U1 = fmul(__ll2float_rn((int64_t)m[0] * r1x + (int64_t)m[1] * r1y + (int64_t)m[2] * r1z), sc);
+    const float V1 = fmul(__ll2float_rn((int64_t)m[3] * r1x + (int64_t)m[4] * r1y + (int64_t)m[5] * r1z), sc);
+    const float Z1 = fmul(__ll2float_rn((int64_t)m[6] * r1x + (int64_t)m[7] * r1y + (int64_t)m[8] * r1z), sc);
+    const float zn = kZNear;
+    const float dZ = fsub(Z1, Z0);
+    float lo = 0.0f, hi = 1.0f;
+    if (Z0 < zn) {
+        if (!(dZ > 0.0f)) return false;
+        lo = fdiv(fsub(zn, Z0), dZ);
+    }
+    if (Z1 < zn) {
+        if (!(dZ < 0.0f)) return false;
+        hi = fdiv(fsub(zn, Z0), dZ);
+    }
+    if (Z0 > zf) {
+        if (!(dZ < 0.0f)) return false;
+        const float l = fdiv(fsub(zf, Z0), dZ);
+        if (l > lo) lo = l;
+    }
+    if (Z1 > zf) {
+        if (!(dZ > 0.0f)) return false;
+        const float h = fdiv(fsub(zf, Z0), dZ);
+        if (h < hi) hi = h;
+    }
+    if (!(lo < hi)) return false;
+    const float dU = fsub(U1, U0), dV = fsub(V1, V0);
+    const float Ua = fadd(U0, fmul(lo, dU)), Va = fadd(V0, fmul(lo, dV)), Za = fadd(Z0, fmul(lo, dZ));
+    const float Ub = fadd(U0, fmul(hi, dU)), Vb = fadd(V0, fmul(hi, dV)), Zb = fadd(Z0, fmul(hi, dZ));
+    if (!(Za > 0.0f && Zb > 0.0f)) return false;
+    g.lo = lo;
+    g.hi = hi;
+    g.Za = Za;
+    g.Zb = Zb;
+    g.ua = fdiv(Ua, Za);
+    g.va = fdiv(Va, Za);
+    g.ub = fdiv(Ub, Zb);
+    g.vb = fdiv(Vb, Zb);
+    g.wa = fdiv(1.0f, Za);
+    g.wb = fdiv(1.0f, Zb);
+    // Liang-Barsky against 0 <= u <= W, 0 <= v <= H (edges in the order -u, +u, -v, +v)
+    const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
+    const float pe[4] = {-du, du, -dv, dv};
+    const float qe[4] = {g.ua, fsub(__int2float_rn(W), g.ua), g.va, fsub(__int2float_rn(H), g.va)};
+    float s0 = 0.0f, s1 = 1.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (pe[e] == 0.0f) {
+            if (qe[e] < 0.0f) return false;
+            continue;
+        }
+        const float r = fdiv(qe[e], pe[e]);
+        if (pe[e] < 0.0f) {
+            if (r > s1) return false;
+            if (r > s0) s0 = r;
+        } else {
+            if (r < s0) return false;
+            if (r < s1) s1 = r;
+        }
+    }
+    if (!(s0 < s1)) return false;
+    g.s0 = s0;
+    g.s1 = s1;
+    return true;
+}
+
+// screen parameter of the ray fraction lam (perspective-correct); false outside the clip
+__device__ __forceinline__ bool seg_param(const Seg &g, float lam, float &s) {
+    if (!(lam >= g.lo && lam <= g.hi)) return false;
+    const float mu = fdiv(fsub(lam, g.lo), fsub(g.hi, g.lo));
+    const float num = fmul(mu, g.Zb);
+    const float den = fadd(fmul(fsub(1.0f, mu), g.Za), num);
+    s = fdiv(num, den);
+    return s >= g.s0 && s < g.s1;
+}
+
+// a voxel's sample: midpoint of the ray's traversal of it (entry ne / ade, exit nx / adx capped at
+// the range) as a fraction of the range T (= Tq / 2^30 in crossing units)
+__device__ __forceinline__ float sample_lambda(uint32_t ne, uint32_t ade, uint32_t nx, uint32_t adx, float T) {
+    const float lin = fdiv(fdiv(__uint2float_rn(ne), __uint2float_rn(ade)), T);
+    float lout = fdiv(fdiv(__uint2float_rn(nx), __uint2float_rn(adx)), T);
+    if (lout > 1.0f) lout = 1.0f;
+    return fmul(fadd(lin, lout), 0.5f);
+}
+
+// step 4 for the samples in `cand` (bit q = pending sample q, screen parameter sv[q * stride]):
+// walks the portions in order; each sample is decided by the first portion containing it and
+// removed from `pend` when that portion is observed. Returns the portions walked.
+__device__ uint32_t seg_walk(const Seg &g, int W, int H, const uint32_t *D, const float *sv, int stride, uint32_t cand,
+                             uint32_t &pend) {
+    const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
+    float s = g.s0;
+    const float fi = floorf(fadd(g.ua, fmul(s, du))), fj = floorf(fadd(g.va, fmul(s, dv)));
+    int i = fi < 0.0f ? 0 : (fi > __int2float_rn(W - 1) ? W - 1 : __float2int_rz(fi));
+    int j = fj < 0.0f ? 0 : (fj > __int2float_rn(H - 1) ? H - 1 : __float2int_rz(fj));
+    const int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
+    float sx = si ? fdiv(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), du) : __int_as_float(0x7f800000);
+    float sy = sj ? fdiv(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), dv) : __int_as_float(0x7f800000);
+    uint32_t walked = 0;
+    for (;;) {
+        float se = sx < sy ? sx : sy;
+        if (g.s1 < se) se = g.s1;
+        ++walked;
+        const float sm = fmul(fadd(s, se), 0.5f);
+        const float zm = fdiv(1.0f, fadd(g.wa, fmul(sm, fsub(g.wb, g.wa))));
+        const float Dv = fmul(__uint2float_rn(__ldg(D + (size_t)j * W + i)), 1.52587890625e-05f);
+        const bool obs = zm <= Dv;
+        for (uint32_t c = cand; c; c &= c - 1) {
+            const int q = __ffs(c) - 1;
+            const float x = sv[q * stride];
+            if (s <= x && x < se) {
+                cand &= ~(1u << q);
+                if (obs) pend &= ~(1u << q);
+            }
+        }
+        if (!cand || !(se < g.s1)) break;
+        if (sx <= sy) {
+            i += si;
+            if (i < 0 || i >= W) break;
+            sx = fdiv(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), du);
+        } else {
+            j += sj;
+            if (j < 0 || j >= H) break;
+            sy = fdiv(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), dv);
+        }
+        s = se;
+    }
+    return walked;
+}
+
+// Exclusion of a lane's pending samples (ray fractions lam[q * stride], q < ns): the union over
+// the ancestors (parent first) of their observed portions. Returns the samples left (marginal).
+template <bool STATS>
+__device__ int flush_samples(const LevelParams &p, const IvAnc *anc, int na, const int64_t P[3], const int64_t E[3],
+                             float zf, const float *lam, float *sv, int stride, int ns, unsigned long long &st_seg,
+                             unsigned long long &st_por) {
+    uint32_t pend = ns >= 32 ? 0xffffffffu : ((1u << ns) - 1u);
+    for (int a = 0; a < na && pend; ++a) {
+        const IvAnc &A = anc[a];
+        Seg g;
+        if constexpr (STATS) ++st_seg;
+        if (!seg_setup(p.yawtab + A.yaw * 12 + 2, make_int3(A.px, A.py, A.pz), P, E, zf, p.W, p.H, g)) continue;
+        uint32_t cand = 0;
+        for (uint32_t c = pend; c; c &= c - 1) {
+            const int q = __ffs(c) - 1;
+            float s;
+            if (seg_param(g, lam[q * stride], s)) {
+                sv[q * stride] = s;
+                cand |= 1u << q;
+            }
+        }
+        if (!cand) continue;
+        const uint32_t w = seg_walk(g, p.W, p.H, A.D, sv, stride, cand, pend);
+        if constexpr (STATS) st_por += w;
+    }
+    return __popc(pend);
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const LevelParams p) {
+    extern __shared__ IvAnc s_iv_anc[];
+    __shared__ float s_lam[kIvChunk][kIvThreads];
+    __shared__ float s_sv[kIvChunk][kIvThreads];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    IvAnc *anc = s_iv_anc + warp * p.max_anc;
+    float *lam = &s_lam[0][threadIdx.x];
+    float *sv = &s_sv[0][threadIdx.x];
+    const int l0 = p.level_off[p.lvl];
+    const int L = p.level_off[p.lvl + 1] - l0;
+    const int items = L * p.K * p.tiles;
+    const float zf = fmul(__ll2float_rn(p.Tq), 1.52587890625e-05f);   // range, voxel units
+    const float T = fmul(__ll2float_rn(p.Tq), 9.313225746154785e-10f);  // range, crossing units
+    unsigned long long st_rays = 0, st_steps = 0, st_unk = 0, st_seg = 0, st_por = 0;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(p.work + p.lvl, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= items) break;
+        int li, k, tile;
+        decode_item(p, c, li, k, tile);
+        const int n = p.level_nodes[l0 + li];
+        const int4 nd = p.node[n];
+        const int2 ar = p.anc_range[n];
+        const int na = min(ar.y, p.max_anc);
+        __syncwarp();
+        for (int t = lane; t < na; t += 32) {
+            const int a = p.anc[ar.x + t];
+            const int4 an = p.node[a];
+            IvAnc r;
+            r.px = an.x;
+            r.py = an.y;
+            r.pz = an.z;
+            r.yaw = p.sel_yaw[a];
+            r.D = p.arena + (size_t)an.w * p.W * p.H;
+            anc[t] = r;
+        }
+        __syncwarp();
+        const int32_t *yk = p.yawtab + k * 12;
+        const int ck = yk[0], sk = yk[1];
+        const int64_t P[3] = {nd.x, nd.y, nd.z};
+        const int tx0 = (tile % p.tiles_x) * p.tile_w, ty0 = (tile / p.tiles_x) * p.tile_h;
+        const int tile_rays = p.tile_w * p.tile_h;
+        int c_abs = 0, c_mrg = 0;
+        for (int idx = lane; idx < tile_rays; idx += 32) {
+            const int ti = tx0 + idx % p.tile_w, tj = ty0 + idx / p.tile_w;
+            if (ti >= p.W || tj >= p.H) continue;
+            const int4 b = p.body[tj * p.W + ti];
+            int dx, dy, dz;
+            ray_dir(b, ck, sk, dx, dy, dz);
+            const int64_t E[3] = {P[0] + (((int64_t)p.Tq * dx) >> 30), P[1] + (((int64_t)p.Tq * dy) >> 30),
+                                  P[2] + (((int64_t)p.Tq * dz) >> 30)};
+            RayIn r;
+            ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
+            if constexpr (STATS) ++st_rays;
+            uint32_t ne = 0, ade = 1;
+            int ns = 0;
+            for (;;) {
+                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+                if constexpr (STATS) ++st_steps;
+                if (code == kOcc) break;
+                uint32_t nx = 0, adx = 1;
+                bool owned = false;
+                if (code == kUnknown) {
+                    if constexpr (STATS) ++st_unk;
+                    // owner test (reading A1): the voxel centre projects into pixel (ti, tj)
+                    const int rx = voxel_offset(r.nx, r.sx), ry = voxel_offset(r.ny, r.sy),
+                              rz = voxel_offset(r.nz, r.sz);
+                    const int64_t Z = (int64_t)yk[8] * rx + (int64_t)yk[9] * ry + (int64_t)yk[10] * rz;
+                    const int64_t U = (int64_t)yk[2] * rx + (int64_t)yk[3] * ry + (int64_t)yk[4] * rz;
+                    const int64_t V = (int64_t)yk[5] * rx + (int64_t)yk[6] * ry + (int64_t)yk[7] * rz;
+                    const int64_t iZ = (int64_t)ti * Z, jZ = (int64_t)tj * Z;
+                    owned = Z > 0 && U >= iZ && U < iZ + Z && V >= jZ && V < jZ + Z;
+                }
+                const bool more = ray_step<true>(r, nx, adx);  // nx / adx: this voxel's exit crossing
+                if (owned) {
+                    ++c_abs;
+                    lam[ns * kIvThreads] = sample_lambda(ne, ade, nx, adx, T);
+                    if (++ns == kIvChunk) {
+                        c_mrg += flush_samples<STATS>(p, anc, na, P, E, zf, lam, sv, kIvThreads, ns, st_seg, st_por);
+                        ns = 0;
+                    }
+                }
+                if (!more) break;
+                ne = nx;
+                ade = adx;
+            }
+            if (ns) c_mrg += flush_samples<STATS>(p, anc, na, P, E, zf, lam, sv, kIvThreads, ns, st_seg, st_por);
+        }
+        c_abs = __reduce_add_sync(0xffffffffu, c_abs);
+        c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);
+        if (lane == 0 && (c_abs | c_mrg)) {
+            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2, c_abs);
+            atomicAdd(p.cnt + ((size_t)n * p.K + k) * 2 + 1, c_mrg);
+        }
+        if constexpr (STATS) {
+            if (lane == 0) atomicAdd(p.stats + 3, (unsigned long long)(uint32_t)c_abs);
+        }
+    }
+    if constexpr (STATS) {
+        atomicAdd(p.stats + 0, st_rays);
+        atomicAdd(p.stats + 1, st_steps);
+        atomicAdd(p.stats + 2, st_unk);
+        atomicAdd(p.stats + 4, st_seg);
+        atomicAdd(p.stats + 5, st_por);
+    }
+}
+
+}  // namespace
+
+// dynamic shared memory: the warps' ancestor records, up to MIG_MAX_DEPTH each
+constexpr size_t kIvMaxDyn = (size_t)kIvWarps * MIG_MAX_DEPTH * sizeof(IvAnc);
+
+void launch_count_interval(const LevelParams &p, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)kIvWarps * (size_t)std::max(1, p.max_anc) * sizeof(IvAnc);
+    if (p.stats) interval_count_kernel<true><<<grid, kIvThreads, smem, s>>>(p);
+    else interval_count_kernel<false><<<grid, kIvThreads, smem, s>>>(p);
+}
+
+// Resident CTAs per SM (for the grid cap); also lifts the kernels' dynamic shared-memory limit to
+// the deepest tree's ancestor records. Called once per context, before any launch.
+int count_interval_ctas_per_sm() {
+    cudaFuncSetAttribute(interval_count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIvMaxDyn);
+    cudaFuncSetAttribute(interval_count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIvMaxDyn);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, interval_count_kernel<false>, kIvThreads,
+                                                  (size_t)kIvWarps * 16 * sizeof(IvAnc));
+    return std::max(1, n);
+}
+
+}  // namespace mig

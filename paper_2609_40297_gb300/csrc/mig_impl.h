@@ -98,6 +98,7 @@ struct mig_ctx {
     mig::DeviceAllocator alloc;
     int num_sms = 0;
     int count_ctas = 1;        // resident count-kernel CTAs per SM
+    int interval_ctas = 1;     // resident interval-mode count CTAs per SM
     std::vector<std::unique_ptr<mig::Camera>> cameras;
     mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
     void *pinned = nullptr;  // pinned host staging

@@ -255,6 +255,23 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = max_over_ranks(float(np.sum(e2e_ms)), dev)
     e2e_value = ws * rays_per_step * len(e2e_ms) / (e2e_total / 1e3)
+    # ---- the gain modes side by side (Table 2's absolute vs marginal columns, and the paper's
+    # screen-space interval overlap against voxel-centre samples), each through the public host-array
+    # call, outside the timed region: median of 3 after one warm-up
+    modes = {}
+    if rank == 0 and not args.no_modes:
+        for name, md in (("marginal_samples", mig.MODE_MARGINAL), ("marginal_intervals", mig.MODE_INTERVAL),
+                         ("single_parent", mig.MODE_SINGLE_PARENT), ("absolute", mig.MODE_ABSOLUTE)):
+            mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+            ts = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+                ts.append((time.perf_counter() - t0) * 1e3)
+            ms = float(np.median(ts))
+            modes[name] = {"ms_per_replan": ms, "rays_per_s": rays_per_step / (ms / 1e3),
+                           "marg_sum": int(g["marg"].sum()), "abs_sum": int(g["abs"].sum())}
     # ---- roofline of the dominant kernel (count pass). It is bound by integer issue: achieved =
     # algorithmic integer operations per launch / average launch time, against the issue ceiling.
     # The gather roofline (algorithmic voxel + depth bytes against HBM) is reported beside it.
@@ -308,6 +325,7 @@ def run_ours(args):
                                 "algorithmic_bytes_per_launch": alg_bytes_launch,
                                 "note": "algorithmic bytes = DDA voxel gathers (1 B) + ancestor depth reads (4 B); "
                                         "ncu: L2 sector hit 99 %, 3.75 sectors per load request"},
+            "modes": modes or None,
             "work_per_step": stats,
             "kernel_ms_per_step": {k.replace("_ms", ""): v / args.steps for k, v in ktimes.items() if k.endswith("_ms")},
             "clocks": clocks,
@@ -529,7 +547,7 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(workload, sample_depth=None, with_gap=False):
+def cpu_baseline(workload, sample_depth=None, with_gap=False, with_interval_gap=False):
     """The oracle as it stands, on this host's cores, on a bounded, ancestor-closed sample of
     the workload (all nodes up to a depth), reported in the benchmark's unit."""
     import oracle
@@ -558,6 +576,16 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False):
         rep = oracle.gap_report(d[sel], db["marg"][sel], ex[sel], abs_gain=db["abs"][sel])
         rep["nodes"] = m
         out["gap_to_exact"] = rep
+        if with_interval_gap:
+            # the same report for the paper's interval overlap (Eq. 5-7), with its own yaws
+            iv = oracle.eval_tree(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent,
+                                  prob.tree.pos, s, node_mask=mask, mode=oracle.MODE_INTERVAL)
+            off, ids = oracle.visible_sets(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.pos,
+                                           iv["yaw"], s, node_mask=mask)
+            exi = oracle.exact_dfs(prob.tree.parent, off, ids, prob.map.grid.size, node_mask=mask)
+            repi = oracle.gap_report(d[sel], iv["marg"][sel], exi[sel], abs_gain=iv["abs"][sel])
+            repi["nodes"] = m
+            out["gap_to_exact_intervals"] = repi
     return out
 
 
@@ -592,6 +620,7 @@ def main():
     ap.add_argument("--workload", default="paper_scale",
                     choices=["paper_scale", "tiny", "large", "batched", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison (interval, absolute)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -608,9 +637,11 @@ def main():
     ws, rank, _ = dist_env()
     if rank == 0 and res is not None:
         if ws == 1 and not args.no_cpu_baseline and args.workload in ("paper_scale", "tiny", "large"):
-            cb = cpu_baseline(args.workload, with_gap=True)
+            cb = cpu_baseline(args.workload, with_gap=True, with_interval_gap=not args.no_modes)
             res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
             res["gap_to_exact"] = cb.get("gap_to_exact")
+            if cb.get("gap_to_exact_intervals"):
+                res["gap_to_exact_intervals"] = cb["gap_to_exact_intervals"]
         print(json.dumps(res))
 
 

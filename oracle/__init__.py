@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "libmig_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL = 0, 1, 2, 3
+MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL, MODE_PANORAMIC = 0, 1, 2, 3, 4
 
 
 _MUTANT = 0  # planted-mistake variant (pin-strength tests only); 0 = the oracle
@@ -81,6 +81,9 @@ def lib():
             i64 = C.c_int64
             L.oracle_sample_lambda.argtypes = [i64, i64, i64, i64, i64]
             L.oracle_sample_lambda.restype = C.c_float
+            L.oracle_pano_tables.argtypes = [f, f, i, i, i, f, p, p, p, p, p]
+            L.oracle_pano_cells.argtypes = [f, f, i, i, i, f, p, i, p, p]
+            L.oracle_pano_node_columns.argtypes = [p, i, i, i, p, f, f, i, i, i, f, C.c_int64, p]
             _lib = L
     return _lib
 
@@ -232,6 +235,51 @@ def sample_lambda(ne, ade, nx, adx, Tq):
     """Interval mode: a voxel's sample, the midpoint of the ray's traversal (entry ne/ade, exit
     nx/adx, capped at the range), as a fraction of the range."""
     return float(lib().oracle_sample_lambda(int(ne), int(ade), int(nx), int(adx), int(Tq)))
+
+
+def pano_tables(sensor):
+    """Panoramic mode tables: dict with A (columns), Wc (columns per yaw window), step (columns per
+    yaw bin), bc [A, 2] (wedge boundary cos/sin, Q30), dirs [A, H, 3] (ray of each cell, Q30),
+    rows [A, 6] (strip rows mv, mz, Q16) and wstart [K] (first column of each yaw's window)."""
+    W, H, K = sensor.width, sensor.height, sensor.yaw_bins
+    dims = np.zeros(3, np.int32)
+    args = (float(sensor.hfov_deg), float(sensor.vfov_deg), W, H, K, float(sensor.pitch_deg))
+    rc = lib().oracle_pano_tables(*args, _ptr(dims), None, None, None, None)
+    if rc != 0:
+        raise OracleError(f"oracle_pano_tables failed: {rc}")
+    A = int(dims[0])
+    bc = np.zeros((A, 2), np.int32)
+    dirs = np.zeros((A, H, 3), np.int32)
+    rows = np.zeros((A, 6), np.int32)
+    ws = np.zeros(K, np.int32)
+    lib().oracle_pano_tables(*args, _ptr(dims), _ptr(bc), _ptr(dirs), _ptr(rows), _ptr(ws))
+    return {"A": A, "Wc": int(dims[1]), "step": int(dims[2]), "bc": bc, "dirs": dirs, "rows": rows, "wstart": ws}
+
+
+def pano_cells(sensor, P, vox):
+    """Owning (column, row) of each voxel seen from P (Q16) by search over every wedge; -1 = none."""
+    vox = _c(vox, np.int32).reshape(-1, 3)
+    out = np.zeros((vox.shape[0], 2), np.int32)
+    rc = lib().oracle_pano_cells(float(sensor.hfov_deg), float(sensor.vfov_deg), sensor.width, sensor.height,
+                                 sensor.yaw_bins, float(sensor.pitch_deg), _ptr(_c(P, np.int64)), vox.shape[0],
+                                 _ptr(vox), _ptr(out))
+    if rc != 0:
+        raise OracleError("oracle_pano_cells failed")
+    return out
+
+
+def pano_node_columns(grid, P, sensor, Tq):
+    """Per-column absolute counts of one node (no ancestors) in the panoramic mode."""
+    grid = _c(grid, np.uint8)
+    nz, ny, nx = grid.shape
+    A = pano_tables(sensor)["A"]
+    out = np.zeros(A, np.int64)
+    rc = lib().oracle_pano_node_columns(_ptr(grid), nx, ny, nz, _ptr(_c(P, np.int64)), float(sensor.hfov_deg),
+                                        float(sensor.vfov_deg), sensor.width, sensor.height, sensor.yaw_bins,
+                                        float(sensor.pitch_deg), int(Tq), _ptr(out))
+    if rc != 0:
+        raise OracleError("oracle_pano_node_columns failed")
+    return out
 
 
 def quantize(pos, origin, voxel, dims):

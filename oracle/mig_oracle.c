@@ -33,7 +33,7 @@ typedef int64_t i64;
 #define OR_OCCUPIED 2
 #define OR_MAX_DEPTH 64
 
-enum { MODE_MARGINAL = 0, MODE_SINGLE_PARENT = 1, MODE_ABSOLUTE = 2, MODE_INTERVAL = 3 };
+enum { MODE_MARGINAL = 0, MODE_SINGLE_PARENT = 1, MODE_ABSOLUTE = 2, MODE_INTERVAL = 3, MODE_PANORAMIC = 4 };
 
 /* Planted mistakes for the pin-strength tests (tests/test_oracle_mutants.py). The default
  * build defines none; each variant .so is built with -DORACLE_MUTANT=<m> and must fail at
@@ -454,6 +454,159 @@ static int interval_visit(void *vctx, const int32_t v[3], uint8_t code, const i6
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------
+ * Panoramic mode: one 360-degree cast per node, then a window sum per yaw bin (the yaw set of
+ * Sec. III-B evaluated from shared rays). The horizon is cut into A azimuth wedges ("columns")
+ * of width 2 pi / A, A = K * ceil(W 360 / (hfov K)) so that a yaw step is a whole number of
+ * columns and a column is no wider than a pinhole pixel at the image centre. Column c holds
+ * the directions with azimuth in [c, c + 1) * 2 pi / A (exact integer test against the wedge's
+ * two boundary vectors, Q30). Each column is a one-pixel-wide strip camera looking along the
+ * wedge's centre azimuth, with the pinhole's rows (Eq. 5's v, focal length and principal point
+ * from the vertical field of view); its rays pass through the strip's row centres. A voxel is
+ * owned by the cell (column, row) containing its centre (the rule of reading A1), counted as
+ * absolute gain for the column, and as marginal gain unless an ancestor's (pinhole) depth
+ * buffer observes it. Yaw k sums the Wc = round(A hfov / 360) columns centred on its azimuth.
+ * Level camera only (pitch 0): wedges are vertical half-planes.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    int A, Wc, step, H;
+    int32_t *bc;   /* A: boundary (cos, sin) of azimuth c 2 pi / A, Q30 */
+    int32_t *dir;  /* A*H*3: ray of cell (c, j), Q30 */
+    int32_t *row;  /* A*6: strip projection rows mv (3), mz (3), Q16 */
+} pano_t;
+
+static void pano_free(pano_t *p) { free(p->bc); free(p->dir); free(p->row); }
+
+static int pano_build(pano_t *p, float hfov, float vfov, int W, int H, int K, float pitch) {
+    memset(p, 0, sizeof(*p));
+    if (W < 1 || H < 1 || W > 2048 || H > 2048 || K < 1 || K > 1024) return -1;
+    if (!(hfov > 0.0f && hfov < 180.0f && vfov > 0.0f && vfov < 180.0f)) return -1;
+    if (pitch != 0.0f) return -1;
+    int step = (int)ceil(((double)W * 360.0) / ((double)hfov * (double)K));
+    if (step < 1) step = 1;
+    int A = step * K;
+    if (A > 65536) return -1;
+    p->A = A; p->step = step; p->H = H;
+    p->Wc = (int)llrint(((double)A * (double)hfov) / 360.0);
+    if (p->Wc < 1) p->Wc = 1;
+    p->bc = malloc((size_t)A * 2 * 4);
+    p->dir = malloc((size_t)A * H * 3 * 4);
+    p->row = malloc((size_t)A * 6 * 4);
+    if (!p->bc || !p->dir || !p->row) { pano_free(p); return -2; }
+    double t_v = tan(((double)vfov * 0.5) * (M_PI / 180.0));
+    double fy = ((double)H * 0.5) / t_v, cyp = (double)H * 0.5;
+    for (int c = 0; c < A; ++c) {
+        double ang = ((2.0 * M_PI) * (double)c) / (double)A;
+        p->bc[2 * c] = q30(cos(ang));
+        p->bc[2 * c + 1] = q30(sin(ang));
+        double th = ((2.0 * M_PI) * ((double)c + 0.5)) / (double)A;
+        double cs = cos(th), sn = sin(th);
+        /* strip camera at azimuth th: ez = (cs, sn, 0), ey = (0, 0, -1) */
+        double mv[3] = {cyp * cs, cyp * sn, -fy};
+        for (int a = 0; a < 3; ++a) if (fabs(mv[a]) * 65536.0 >= 2147483647.0) { pano_free(p); return -1; }
+        p->row[6 * c] = q16(mv[0]); p->row[6 * c + 1] = q16(mv[1]); p->row[6 * c + 2] = q16(mv[2]);
+        p->row[6 * c + 3] = q16(cs); p->row[6 * c + 4] = q16(sn); p->row[6 * c + 5] = 0;
+        for (int j = 0; j < H; ++j) {
+            double b = ((double)(2 * j + 1 - H) / (double)H) * t_v;
+            double nrm = sqrt(b * b + 1.0);
+            int32_t *o = p->dir + ((size_t)c * H + j) * 3;
+            o[0] = q30(cs / nrm);
+            o[1] = q30(sn / nrm);
+            o[2] = q30(-b / nrm);
+        }
+    }
+    return 0;
+}
+
+/* the cell (column, row) owning voxel v seen from P (Q16); 0 if none (on the vertical axis,
+ * behind the strip or outside its rows) */
+static int pano_cell(const pano_t *p, const i64 P[3], const int32_t v[3], int *cc, int *jj) {
+    i64 r[3];
+    for (int a = 0; a < 3; ++a) r[a] = (i64)v[a] * ONE_Q16 + ONE_Q16 / 2 - P[a];
+    /* column: the wedge c with cross(b_c, r) >= 0 > cross(b_{c+1}, r) */
+    int c = -1;
+    for (int q = 0; q < p->A; ++q) {
+        const int32_t *b0 = p->bc + 2 * q, *b1 = p->bc + 2 * ((q + 1) % p->A);
+        i64 x0 = (i64)b0[0] * r[1] - (i64)b0[1] * r[0];
+        i64 x1 = (i64)b1[0] * r[1] - (i64)b1[1] * r[0];
+        if (x0 >= 0 && (MUT(18) ? x1 <= 0 : x1 < 0)) { c = q; break; }
+    }
+    if (c < 0) return 0;
+    const int32_t *m = p->row + 6 * c;
+    i64 V = (i64)m[0] * r[0] + (i64)m[1] * r[1] + (i64)m[2] * r[2];
+    i64 Z = (i64)m[3] * r[0] + (i64)m[4] * r[1] + (i64)m[5] * r[2];
+    if (Z <= 0) return 0;
+    i64 j = floor_div(V, Z);
+    if (j < 0 || j >= p->H) return 0;
+    *cc = c;
+    *jj = (int)j;
+    return 1;
+}
+
+/* is voxel v (seen from P) in cell (c, j)? the wedge test against column c's two boundaries */
+static int pano_owned(const pano_t *p, int c, int j, const i64 P[3], const int32_t v[3]) {
+    i64 r[3];
+    for (int a = 0; a < 3; ++a) r[a] = (i64)v[a] * ONE_Q16 + ONE_Q16 / 2 - P[a];
+    const int32_t *b0 = p->bc + 2 * c, *b1 = p->bc + 2 * ((c + 1) % p->A);
+    i64 x0 = (i64)b0[0] * r[1] - (i64)b0[1] * r[0];
+    i64 x1 = (i64)b1[0] * r[1] - (i64)b1[1] * r[0];
+    if (!(x0 >= 0 && (MUT(18) ? x1 <= 0 : x1 < 0))) return 0;
+    const int32_t *m = p->row + 6 * c;
+    i64 V = (i64)m[0] * r[0] + (i64)m[1] * r[1] + (i64)m[2] * r[2];
+    i64 Z = (i64)m[3] * r[0] + (i64)m[4] * r[1] + (i64)m[5] * r[2];
+    return Z > 0 && floor_div(V, Z) == j;
+}
+
+/* first column of yaw k's window */
+static int pano_window_start(const pano_t *p, int k) {
+    int s0 = k * p->step - p->Wc / 2 + (MUT(19) ? 1 : 0);
+    return ((s0 % p->A) + p->A) % p->A;
+}
+
+typedef struct {
+    const pano_t *pano;
+    const cam_t *cam;
+    int c, j;
+    const i64 *P;
+    int n_anc;
+    const i64 (*anc_P)[3];
+    const int *anc_yaw;
+    uint32_t *const *anc_D;
+    i64 abs_count, marg_count;
+} pano_ctx;
+
+static int pano_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 te[2], const i64 tx[2]) {
+    (void)te;
+    (void)tx;
+    pano_ctx *x = (pano_ctx *)vctx;
+    if (code != OR_UNKNOWN) return 0;
+    if (!pano_owned(x->pano, x->c, x->j, x->P, v)) return 0;
+    x->abs_count++;
+    for (int a = 0; a < x->n_anc; ++a)
+        if (observed_by(x->cam, x->anc_P[a], x->anc_yaw[a], x->anc_D[a], v)) return 0;
+    x->marg_count++;
+    return 0;
+}
+
+/* per-column counts of one node: cast every cell's ray once */
+static void pano_columns(const pano_t *pano, const cam_t *cam, const grid_t *G, const i64 P[3], i64 Tq, int na,
+                         const i64 (*anc_P)[3], const int *anc_yaw, uint32_t *const *anc_D, i64 *col_abs,
+                         i64 *col_marg) {
+    pano_ctx x = {pano, cam, 0, 0, P, na, anc_P, anc_yaw, anc_D, 0, 0};
+    for (int c = 0; c < pano->A; ++c) {
+        x.abs_count = x.marg_count = 0;
+        x.c = c;
+        for (int j = 0; j < pano->H; ++j) {
+            const int32_t *o = pano->dir + ((size_t)c * pano->H + j) * 3;
+            i64 d[3] = {o[0], o[1], o[2]};
+            x.j = j;
+            dda(G, P, d, Tq, ONE_Q30, pano_visit, &x, NULL);
+        }
+        col_abs[c] = x.abs_count;
+        col_marg[c] = x.marg_count;
+    }
+}
+
 static int quantize_pos(const float *pos, const float origin[3], float voxel, const int dims[3], i64 P[3]) {
     for (int a = 0; a < 3; ++a) {
         double q = (((double)pos[a] - (double)origin[a]) / (double)voxel) * 65536.0;
@@ -492,7 +645,7 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
                      int32_t *cnt_abs, int32_t *cnt_marg, uint32_t *depth_out, int n_threads) {
     if (n < 0 || nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return -1;
     if (!(voxel > 0.0f)) return -1;
-    if (mode < 0 || mode > 3) return -1;
+    if (mode < 0 || mode > 4) return -1;
     if (n == 0) return 0;
     for (size_t i = 0, m = (size_t)nx * ny * nz; i < m; ++i)
         if (grid[i] > OR_OCCUPIED) return -1;
@@ -501,6 +654,9 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
     if (rc) return rc;
     i64 Tq = llrint(((double)range_m / (double)voxel) * 65536.0);
     if (Tq < 1 || Tq > 1024 * ONE_Q16) { cam_free(&cam); return -1; }
+    pano_t pano;
+    memset(&pano, 0, sizeof(pano));
+    if (mode == MODE_PANORAMIC && (rc = pano_build(&pano, hfov, vfov, W, H, K, pitch)) != 0) { cam_free(&cam); return rc; }
     grid_t G = {grid, {nx, ny, nz}};
     int dims[3] = {nx, ny, nz};
     int32_t *depth = malloc((size_t)n * 4);
@@ -529,6 +685,39 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
         int L = 0;
         for (int i = 0; i < n; ++i)
             if (depth[i] == d && (!node_mask || node_mask[i])) lvl[L++] = i;
+        if (mode == MODE_PANORAMIC) {
+            /* one 360-degree cast per node, per-column counts, then each yaw's window sum */
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int li = 0; li < L; ++li) {
+                int nd = lvl[li];
+                i64 anc_P[OR_MAX_DEPTH][3];
+                int anc_yaw[OR_MAX_DEPTH];
+                uint32_t *anc_D[OR_MAX_DEPTH];
+                int na = 0;
+                for (int p = parent[nd]; p >= 0; p = parent[p]) {
+                    memcpy(anc_P[na], P[p], sizeof(anc_P[na]));
+                    anc_yaw[na] = yaw[p];
+                    anc_D[na] = Dn[p];
+                    na++;
+                }
+                i64 *ca = malloc((size_t)pano.A * 8), *cm = malloc((size_t)pano.A * 8);
+                if (!ca || !cm) { rc = -2; free(ca); free(cm); continue; }
+                pano_columns(&pano, &cam, &G, P[nd], Tq, na, (const i64(*)[3])anc_P, anc_yaw, anc_D, ca, cm);
+                for (int k = 0; k < K; ++k) {
+                    i64 sa = 0, sm = 0;
+                    int c0 = pano_window_start(&pano, k);
+                    for (int q = 0; q < pano.Wc; ++q) {
+                        int c = (c0 + q) % pano.A;
+                        sa += ca[c];
+                        sm += cm[c];
+                    }
+                    cabs[(size_t)nd * K + k] = (int32_t)sa;
+                    cmarg[(size_t)nd * K + k] = (int32_t)sm;
+                }
+                free(ca);
+                free(cm);
+            }
+        } else
         /* counts for every (node of the level, yaw) */
 #pragma omp parallel for collapse(2) schedule(dynamic, 1)
         for (int li = 0; li < L; ++li) {
@@ -641,6 +830,7 @@ done:
     if (Dn) for (int i = 0; i < n; ++i) free(Dn[i]);
     free(Dn); free(depth); free(P); free(yaw); free(cabs); free(cmarg);
     cam_free(&cam);
+    pano_free(&pano);
     return rc;
 }
 
@@ -782,6 +972,56 @@ int oracle_ray_intervals(float hfov, float vfov, int W, int H, int K, float pitc
 float oracle_sample_lambda(int64_t ne, int64_t ade, int64_t nx, int64_t adx, int64_t Tq) {
     const i64 te[2] = {ne, ade}, tx[2] = {nx, adx};
     return sample_lambda(te, tx, Tq);
+}
+
+/* panoramic tables (for pins): dims[3] = A, Wc, step; bc[A*2], dirs[A*H*3], rows[A*6],
+ * wstart[K] = first column of each yaw's window */
+int oracle_pano_tables(float hfov, float vfov, int W, int H, int K, float pitch, int32_t *dims, int32_t *bc,
+                       int32_t *dirs, int32_t *rows, int32_t *wstart) {
+    pano_t p;
+    int rc = pano_build(&p, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    dims[0] = p.A; dims[1] = p.Wc; dims[2] = p.step;
+    if (bc) memcpy(bc, p.bc, (size_t)p.A * 2 * 4);
+    if (dirs) memcpy(dirs, p.dir, (size_t)p.A * H * 3 * 4);
+    if (rows) memcpy(rows, p.row, (size_t)p.A * 6 * 4);
+    if (wstart) for (int k = 0; k < K; ++k) wstart[k] = pano_window_start(&p, k);
+    pano_free(&p);
+    return 0;
+}
+
+/* owning cell (c, j) of each voxel seen from P, by search over all wedges (-1, -1: none) */
+int oracle_pano_cells(float hfov, float vfov, int W, int H, int K, float pitch, const int64_t *P, int nv,
+                      const int32_t *vox, int32_t *out) {
+    pano_t p;
+    int rc = pano_build(&p, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    for (int i = 0; i < nv; ++i) {
+        int c = -1, j = -1;
+        if (!pano_cell(&p, P, vox + 3 * (size_t)i, &c, &j)) c = j = -1;
+        out[2 * (size_t)i] = c;
+        out[2 * (size_t)i + 1] = j;
+    }
+    pano_free(&p);
+    return 0;
+}
+
+/* per-column absolute counts of one node with no ancestors (for pins) */
+int oracle_pano_node_columns(const uint8_t *grid, int nx, int ny, int nz, const int64_t *P, float hfov, float vfov,
+                             int W, int H, int K, float pitch, int64_t Tq, int64_t *col_abs) {
+    pano_t p;
+    int rc = pano_build(&p, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    cam_t c;
+    if ((rc = cam_build(&c, hfov, vfov, W, H, K, pitch)) != 0) { pano_free(&p); return rc; }
+    grid_t G = {grid, {nx, ny, nz}};
+    i64 *cm = malloc((size_t)p.A * 8);
+    if (!cm) { pano_free(&p); cam_free(&c); return -2; }
+    pano_columns(&p, &c, &G, P, Tq, 0, NULL, NULL, NULL, col_abs, cm);
+    free(cm);
+    pano_free(&p);
+    cam_free(&c);
+    return 0;
 }
 
 int oracle_quantize(const float *pos, int n, const float *origin, float voxel, int nx, int ny, int nz, int64_t *P) {

@@ -6,15 +6,18 @@ inclusive range test, exit instead of entry depth, no owner test, parent-only ex
 a strict depth comparison, highest-index yaw ties, a flipped yaw sign, an exact route
 that double counts, and in the interval mode (Eq. 5-7): a depth sample at the portion's
 entry instead of its midpoint, a screen parameter without perspective correction, a strict
-depth comparison, and a voxel sample at the voxel's entry instead of its traversal midpoint."""
+depth comparison, and a voxel sample at the voxel's entry instead of its traversal midpoint;
+in the panoramic mode: a wedge test that includes its upper boundary (double ownership) and
+a yaw window shifted by one column."""
 import pytest
 
 import oracle
 import test_oracle_interval as ipins  # noqa: E402
+import test_oracle_pano as ppins  # noqa: E402
 import test_oracle_pins as pins  # noqa: E402
 from synth import Sensor
 
-MUTANTS = list(range(1, 18))
+MUTANTS = list(range(1, 20))
 
 PIN_CALLS = [
     lambda o: pins.test_dda_matches_exact_slab_brute_force(o),
@@ -41,6 +44,11 @@ PIN_CALLS = [
     lambda o: ipins.test_interval_mode_invariants(o, 1),
     lambda o: ipins.test_interval_mode_special_cases(o),
     lambda o: ipins.test_interval_mode_gap_to_exact_tiny(o),
+    lambda o: ppins.test_pano_tables_match_float_model(o, ppins.SENSORS[0]),
+    lambda o: ppins.test_pano_cells_match_float_azimuth_elevation(o, ppins.SENSORS[0]),
+    lambda o: ppins.test_pano_owner_set_equals_voxel_centric_brute_force(o, 3),
+    lambda o: ppins.test_pano_window_sums_and_identity(o, ppins.SENSORS[2]),
+    lambda o: ppins.test_pano_mode_invariants(o, 1),
 ]
 
 

@@ -39,6 +39,7 @@ extern "C" {
 #define MIG_MAX_IMAGE 2048      /* rays (pixels) per image axis */
 #define MIG_MAX_YAW_BINS 1024
 #define MIG_MAX_RANGE_VOXELS 1024
+#define MIG_MAX_PANO_COLUMNS 65536 /* azimuth columns of the panoramic mode */
 
 typedef enum {
     MIG_OK = 0,
@@ -81,13 +82,24 @@ typedef struct mig_sensor {
  * valid depth range, projected, clipped to the buffer (Liang-Barsky) and walked pixel by pixel
  * (2D DDA), one inverse-depth sample per visited pixel (Eq. 6); an owned unknown voxel, sampled
  * at the midpoint of the ray's traversal of it, is excluded when it falls in an observed
- * portion of any ancestor. Accepted by mig_tree_eval_ex (and mig_tree_eval_stats) only; the
- * batched, served and device-resident entry points return MIG_EINVAL for it. */
+ * portion of any ancestor.
+ * MIG_MODE_PANORAMIC evaluates the yaw set from one 360-degree cast per node instead of one
+ * pinhole cast per yaw: A = K * ceil(W 360 / (hfov K)) azimuth wedges ("columns"), each a
+ * one-pixel-wide strip camera with the pinhole's H rows; owned unknown voxels are counted per
+ * column (owner = the cell containing the voxel centre), excluded by the ancestors' pinhole
+ * depth buffers as in the marginal mode, and yaw k's gain is the sum over the
+ * round(A hfov / 360) columns centred on its azimuth. The selected yaw's pinhole depth buffer is
+ * rendered for the descendants. Its gains differ from the pinhole modes (different ray geometry).
+ * Needs pitch 0 and at most MIG_MAX_PANO_COLUMNS columns (else MIG_EINVAL).
+ * MIG_MODE_INTERVAL and MIG_MODE_PANORAMIC are accepted by mig_tree_eval_ex (and
+ * mig_tree_eval_stats) only; the batched, served and device-resident entry points return
+ * MIG_EINVAL for them. */
 typedef enum {
     MIG_MODE_MARGINAL = 0,
     MIG_MODE_SINGLE_PARENT = 1,
     MIG_MODE_ABSOLUTE = 2,
-    MIG_MODE_INTERVAL = 3
+    MIG_MODE_INTERVAL = 3,
+    MIG_MODE_PANORAMIC = 4
 } mig_mode;
 
 /* ---------------------------------------------------------------------------------------

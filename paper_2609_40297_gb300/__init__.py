@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmig.so")
 
 MIG_OK, MIG_EINVAL, MIG_ENOMEM, MIG_ECUDA, MIG_ETIMEOUT, MIG_EBUSY, MIG_ENOTFOUND = range(7)
-MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL = 0, 1, 2, 3
+MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL, MODE_PANORAMIC = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "MIG_OK", 1: "MIG_EINVAL", 2: "MIG_ENOMEM", 3: "MIG_ECUDA", 4: "MIG_ETIMEOUT", 5: "MIG_EBUSY",
                 6: "MIG_ENOTFOUND"}
 

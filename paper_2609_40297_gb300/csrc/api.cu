@@ -10,6 +10,7 @@
 #include "interval.h"
 #include "kernels.h"
 #include "mig_impl.h"
+#include "pano.h"
 
 namespace mig {
 
@@ -105,6 +106,34 @@ mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out) {
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // host tables may move with the vector
     *out = cam.get();
     ctx->cameras.push_back(std::move(cam));
+    return MIG_OK;
+}
+
+// The panoramic tables of a context's camera, built and uploaded on first use.
+static mig_status ctx_pano(mig_ctx *ctx, const Camera *ccam) {
+    Camera *cam = nullptr;
+    for (auto &c : ctx->cameras)
+        if (c.get() == ccam) cam = c.get();
+    if (!cam) return fail(MIG_EINVAL, "panoramic mode: unknown camera");
+    if (cam->d_pano_dir) return MIG_OK;
+    mig_status st = pano_build(*cam);
+    if (st != MIG_OK) return st;
+    const size_t bb = cam->pano_bc.size() * 4, db = cam->pano_dir.size() * 4, rb = cam->pano_row.size() * 4;
+    int32_t *b = (int32_t *)ctx->alloc.alloc(bb, ctx->stream), *d = (int32_t *)ctx->alloc.alloc(db, ctx->stream),
+            *r = (int32_t *)ctx->alloc.alloc(rb, ctx->stream);
+    if (!b || !d || !r) {
+        ctx->alloc.free(b, bb, ctx->stream);
+        ctx->alloc.free(d, db, ctx->stream);
+        ctx->alloc.free(r, rb, ctx->stream);
+        return fail(MIG_ENOMEM, "panoramic table allocation failed");
+    }
+    MIG_CUDA_TRY(cudaMemcpyAsync(b, cam->pano_bc.data(), bb, cudaMemcpyHostToDevice, ctx->stream));
+    MIG_CUDA_TRY(cudaMemcpyAsync(d, cam->pano_dir.data(), db, cudaMemcpyHostToDevice, ctx->stream));
+    MIG_CUDA_TRY(cudaMemcpyAsync(r, cam->pano_row.data(), rb, cudaMemcpyHostToDevice, ctx->stream));
+    MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cam->d_pano_bc = b;
+    cam->d_pano_dir = d;
+    cam->d_pano_row = r;
     return MIG_OK;
 }
 
@@ -213,6 +242,7 @@ mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocat
     MIG_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     ctx->count_ctas = count_ctas_per_sm();
     ctx->interval_ctas = count_interval_ctas_per_sm();
+    ctx->pano_ctas = pano_ctas_per_sm();
     ctx->d_err = (int32_t *)ctx->alloc.alloc(256, ctx->stream);
     if (!ctx->d_err) return fail(MIG_ENOMEM, "ctx_create: allocation failed");
     MIG_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream));
@@ -231,6 +261,9 @@ void mig_ctx_destroy(mig_ctx *ctx) {
     for (auto &c : ctx->cameras) {
         ctx->alloc.free(c->d_body, c->body.size() * 4, ctx->stream);
         ctx->alloc.free(c->d_yaw, c->yaw.size() * 4, ctx->stream);
+        ctx->alloc.free(c->d_pano_bc, c->pano_bc.size() * 4, ctx->stream);
+        ctx->alloc.free(c->d_pano_dir, c->pano_dir.size() * 4, ctx->stream);
+        ctx->alloc.free(c->d_pano_row, c->pano_row.size() * 4, ctx->stream);
     }
     ctx->alloc.free(ctx->ws.ptr, ctx->ws.bytes, ctx->stream);
     ctx->alloc.free(ctx->d_err, 256, ctx->stream);
@@ -425,7 +458,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     if (n < 0) return fail(MIG_EINVAL, "tree_eval: negative node count");
     if (n > 0 && (!abs_gain || !marg_gain || !best_yaw)) return fail(MIG_EINVAL, "tree_eval: output array is NULL");
     const int mode = opts ? opts->mode : MIG_MODE_MARGINAL;
-    if (mode < 0 || mode > MIG_MODE_INTERVAL) return fail(MIG_EINVAL, "tree_eval: unknown mode");
+    if (mode < 0 || mode > MIG_MODE_PANORAMIC) return fail(MIG_EINVAL, "tree_eval: unknown mode");
     mig_status st = sensor_check(*sensor, m->voxel);
     if (st != MIG_OK) return st;
     if (n == 0) return MIG_OK;
@@ -445,6 +478,11 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     const Camera *cam = nullptr;
     st = ctx_camera(ctx, *sensor, &cam);
     if (st != MIG_OK) return st;
+    const bool pano = mode == MIG_MODE_PANORAMIC;
+    if (pano) {
+        st = ctx_pano(ctx, cam);
+        if (st != MIG_OK) return st;
+    }
     const int K = cam->K, L = plan.max_depth + 1;
     const size_t WH = (size_t)cam->W * cam->H;
     // device layout: [upload prefix | sel_yaw | out | cnt | arena]
@@ -457,6 +495,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     const size_t o_work = cv.take<int32_t>(L);
     const size_t o_arena = cv.take<uint32_t>((size_t)std::max(1, plan.n_internal) * WH);
     const size_t o_stats = cv.take<unsigned long long>(8);
+    const size_t o_pcnt = cv.take<int32_t>(pano ? (size_t)n * cam->pano_A * 2 : 1);
     char *dev = nullptr;
     st = ctx_workspace(ctx, cv.off, (void **)&dev);
     if (st != MIG_OK) return st;
@@ -492,6 +531,15 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = mode;
     p.max_anc = std::max(1, plan.max_depth);
+    if (pano) {
+        p.pano_A = cam->pano_A;
+        p.pano_Wc = cam->pano_Wc;
+        p.pano_step = cam->pano_step;
+        p.pano_bc = (const int2 *)cam->d_pano_bc;
+        p.pano_dir = (const int4 *)cam->d_pano_dir;
+        p.pano_row = (const int4 *)cam->d_pano_row;
+        p.pano_cnt = (int32_t *)(dev + o_pcnt);
+    }
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
@@ -504,13 +552,21 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         const int Ld = plan.level_off[d + 1] - plan.level_off[d];
         const int items = Ld * K * p.tiles;
         const int cgrid = std::max(1, std::min((items + 7) / 8, count_cap));
-        if (mode == MIG_MODE_INTERVAL)
+        if (mode == MIG_MODE_INTERVAL) {
             timed_launch(ctx, kProfCount, [&] {
                 launch_count_interval(p, std::max(1, std::min((items + 7) / 8, ctx->num_sms * ctx->interval_ctas)),
                                       ctx->stream);
             });
-        else
+        } else if (pano) {
+            const int pitems = Ld * cam->pano_A;
+            timed_launch(ctx, kProfCount, [&] {
+                launch_pano_count(p, std::max(1, std::min((pitems + 7) / 8, ctx->num_sms * ctx->pano_ctas)),
+                                  ctx->stream);
+                launch_pano_window(p, std::max(1, std::min((Ld * K + 255) / 256, 1024)), ctx->stream);
+            });
+        } else {
             timed_launch(ctx, kProfCount, [&] { launch_count(p, cgrid, ctx->stream); });
+        }
         timed_launch(ctx, kProfSelect,
                      [&] { launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), ctx->stream); });
         const int ritems = plan.level_int[d] * render_tiles(p.W, p.H);

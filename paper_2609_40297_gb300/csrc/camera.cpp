@@ -83,4 +83,55 @@ mig_status camera_build(const mig_sensor &s, Camera &c) {
     return MIG_OK;
 }
 
+// Panoramic tables: one 360-degree cast per node. The horizon is cut into A = K * step azimuth
+// wedges, step = ceil(W 360 / (hfov K)), so that a yaw step is a whole number of columns and a
+// column is no wider than a pinhole pixel at the image centre; yaw k's window is the
+// Wc = round(A hfov / 360) columns centred on its azimuth. Column c is a one-pixel-wide strip
+// camera looking along the wedge's centre azimuth with the pinhole's rows.
+mig_status pano_build(Camera &c) {
+    const mig_sensor &s = c.s;
+    if (s.pitch_deg != 0.0f) return fail(MIG_EINVAL, "panoramic mode: the camera must be level (pitch 0)");
+    int step = (int)std::ceil(((double)s.width * 360.0) / ((double)s.hfov_deg * (double)s.yaw_bins));
+    if (step < 1) step = 1;
+    const int A = step * s.yaw_bins, H = s.height;
+    if (A > MIG_MAX_PANO_COLUMNS) return fail(MIG_EINVAL, "panoramic mode: too many azimuth columns");
+    int Wc = (int)std::llrint(((double)A * (double)s.hfov_deg) / 360.0);
+    if (Wc < 1) Wc = 1;
+    const double t_v = std::tan(((double)s.vfov_deg * 0.5) * (M_PI / 180.0));
+    const double fy = ((double)H * 0.5) / t_v, cyp = (double)H * 0.5;
+    c.pano_bc.assign((size_t)A * 2, 0);
+    c.pano_dir.assign((size_t)A * H * 4, 0);
+    c.pano_row.assign((size_t)A * 8, 0);
+    for (int col = 0; col < A; ++col) {
+        const double ang = ((2.0 * M_PI) * (double)col) / (double)A;
+        c.pano_bc[2 * (size_t)col] = q30(std::cos(ang));
+        c.pano_bc[2 * (size_t)col + 1] = q30(std::sin(ang));
+        const double th = ((2.0 * M_PI) * ((double)col + 0.5)) / (double)A;
+        const double cs = std::cos(th), sn = std::sin(th);
+        const double mv[3] = {cyp * cs, cyp * sn, -fy};
+        for (int a = 0; a < 3; ++a)
+            if (std::fabs(mv[a]) * 65536.0 >= 2147483647.0)
+                return fail(MIG_EINVAL, "sensor: focal length too large for the Q16 projection rows");
+        int32_t *r = &c.pano_row[(size_t)col * 8];
+        r[0] = q16(mv[0]);
+        r[1] = q16(mv[1]);
+        r[2] = q16(mv[2]);
+        r[3] = q16(cs);
+        r[4] = q16(sn);
+        r[5] = 0;
+        for (int j = 0; j < H; ++j) {
+            const double b = ((double)(2 * j + 1 - H) / (double)H) * t_v;
+            const double nrm = std::sqrt(b * b + 1.0);
+            int32_t *o = &c.pano_dir[((size_t)col * H + j) * 4];
+            o[0] = q30(cs / nrm);
+            o[1] = q30(sn / nrm);
+            o[2] = q30(-b / nrm);
+        }
+    }
+    c.pano_A = A;
+    c.pano_Wc = Wc;
+    c.pano_step = step;
+    return MIG_OK;
+}
+
 }  // namespace mig

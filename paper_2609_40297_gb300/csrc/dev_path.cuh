@@ -329,6 +329,31 @@ __device__ __forceinline__ int4 lds128(const int4 *ptr) {
     return v;
 }
 
+// The warp's ancestor records of a node (ancestor list ar = (offset, count), na of them, parent
+// first), filled by the lanes together; a warp barrier before and after.
+__device__ __forceinline__ void fill_anc_records(const LevelParams &p, int2 ar, int na, AncRec *anc, int lane) {
+    __syncwarp();
+    for (int t = lane; t < na; t += 32) {
+        const int a = p.anc[ar.x + t];
+        const int4 an = p.node[a];
+        const int y = p.sel_yaw[a];
+        const int32_t *yr = p.yawtab + y * 12;
+        AncRec r;
+        r.px = an.x;
+        r.py = an.y;
+        r.pz = an.z;
+        r.yaw = y;
+        r.fx = (float)an.x * (1.0f / 65536.0f) - 0.5f;
+        r.fy = (float)an.y * (1.0f / 65536.0f) - 0.5f;
+        r.fz = (float)an.z * (1.0f / 65536.0f) - 0.5f;
+#pragma unroll
+        for (int qq = 0; qq < 9; ++qq) r.m[qq] = (float)yr[2 + qq] * (1.0f / 65536.0f);
+        r.D = p.arena + (size_t)an.w * p.W * p.H;
+        anc[t] = r;
+    }
+    __syncwarp();
+}
+
 // Queue key of an owned sample: voxel coordinates (16 bits each) recovered from the voxel-centre
 // offsets (Q16) and the ray origin o (Q16, o.x / o.y / o.z).
 __device__ __forceinline__ unsigned long long sample_key(int rx, int ry, int rz, const int4 o) {
@@ -351,26 +376,7 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
     if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
     else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
     na = min(na, p.max_anc);  // the plan bounds depth by max_anc; this keeps the records in bounds
-    __syncwarp();
-    for (int t = lane; t < na; t += 32) {
-        const int a = p.anc[ar.x + t];
-        const int4 an = p.node[a];
-        const int y = p.sel_yaw[a];
-        const int32_t *yr = p.yawtab + y * 12;
-        AncRec r;
-        r.px = an.x;
-        r.py = an.y;
-        r.pz = an.z;
-        r.yaw = y;
-        r.fx = (float)an.x * (1.0f / 65536.0f) - 0.5f;
-        r.fy = (float)an.y * (1.0f / 65536.0f) - 0.5f;
-        r.fz = (float)an.z * (1.0f / 65536.0f) - 0.5f;
-#pragma unroll
-        for (int qq = 0; qq < 9; ++qq) r.m[qq] = (float)yr[2 + qq] * (1.0f / 65536.0f);
-        r.D = p.arena + (size_t)an.w * p.W * p.H;
-        anc[t] = r;
-    }
-    __syncwarp();
+    fill_anc_records(p, ar, na, anc, lane);
     const int32_t *yk = p.yawtab + k * 12;
 #if MIG_CAM_SMEM
     if (lane == 0) {

@@ -37,6 +37,12 @@ struct LevelParams {
     int lvl;
     unsigned long long *stats;  // NULL, or 8 counters (instrumented pass)
     int max_anc;                // ancestor records per warp (>= the deepest node's depth, <= 64)
+    // panoramic mode: A wedges ("columns") of `pano_step` per yaw bin, Wc columns per yaw window
+    int pano_A, pano_Wc, pano_step;
+    const int2 *pano_bc;        // A: wedge boundary cos, sin (Q30)
+    const int4 *pano_dir;       // A*H: ray of cell (column, row) (Q30), pad
+    const int4 *pano_row;       // A*2: strip rows (mv0 mv1 mv2 mz0) (mz1 mz2 - -) (Q16)
+    int32_t *pano_cnt;          // n*A*2 (abs, excl) per column
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);

@@ -55,8 +55,16 @@ struct Camera {
     std::vector<int32_t> yaw;   // K*kYawRec
     int32_t *d_body = nullptr;
     int32_t *d_yaw = nullptr;
+    // panoramic mode (built on first use; level camera only): A azimuth wedges of a yaw step's
+    // `pano_step` columns each, Wc columns per yaw window
+    int pano_A = 0, pano_Wc = 0, pano_step = 0;
+    std::vector<int32_t> pano_bc;   // A*2: wedge boundary cos, sin (Q30)
+    std::vector<int32_t> pano_dir;  // A*H*4: ray of cell (c, j) (Q30), pad
+    std::vector<int32_t> pano_row;  // A*8: strip rows mv[3], mz[3] (Q16), pad[2]
+    int32_t *d_pano_bc = nullptr, *d_pano_dir = nullptr, *d_pano_row = nullptr;
 };
 mig_status camera_build(const mig_sensor &s, Camera &out);
+mig_status pano_build(Camera &c);  // fills the pano_* host tables (MIG_EINVAL unless pitch is 0)
 mig_status sensor_check(const mig_sensor &s, float voxel);
 int64_t range_q16(float range_m, float voxel);
 
@@ -99,6 +107,7 @@ struct mig_ctx {
     int num_sms = 0;
     int count_ctas = 1;        // resident count-kernel CTAs per SM
     int interval_ctas = 1;     // resident interval-mode count CTAs per SM
+    int pano_ctas = 1;         // resident panoramic count CTAs per SM
     std::vector<std::unique_ptr<mig::Camera>> cameras;
     mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
     void *pinned = nullptr;  // pinned host staging

@@ -107,6 +107,6 @@ def test_interval_mode_rejected_where_unsupported(ctx):
             mig.tree_eval_batch(ctx, [(p.tree.parent, p.tree.pos, p.sensor)], [m], mode=MODE)
         assert e.value.status == mig.MIG_EINVAL
         with pytest.raises(mig.MigError):
-            mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=4)
+            mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=5)
     finally:
         m.close()

@@ -91,9 +91,9 @@ typedef struct mig_sensor {
  * round(A hfov / 360) columns centred on its azimuth. The selected yaw's pinhole depth buffer is
  * rendered for the descendants. Its gains differ from the pinhole modes (different ray geometry).
  * Needs pitch 0 and at most MIG_MAX_PANO_COLUMNS columns (else MIG_EINVAL).
- * MIG_MODE_INTERVAL and MIG_MODE_PANORAMIC are accepted by mig_tree_eval_ex (and
- * mig_tree_eval_stats) only; the batched, served and device-resident entry points return
- * MIG_EINVAL for them. */
+ * The mode is chosen per call by mig_tree_eval_ex, and per tree by mig_tree_eval_batch and
+ * mig_server_submit (a batch holding an interval or panoramic tree runs on the stream-chain
+ * engine); the device-resident entry points and mig_tree_eval_stats evaluate the marginal mode. */
 typedef enum {
     MIG_MODE_MARGINAL = 0,
     MIG_MODE_SINGLE_PARENT = 1,

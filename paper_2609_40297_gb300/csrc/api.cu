@@ -110,7 +110,7 @@ mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out) {
 }
 
 // The panoramic tables of a context's camera, built and uploaded on first use.
-static mig_status ctx_pano(mig_ctx *ctx, const Camera *ccam) {
+mig_status ctx_pano(mig_ctx *ctx, const Camera *ccam) {
     Camera *cam = nullptr;
     for (auto &c : ctx->cameras)
         if (c.get() == ccam) cam = c.get();
@@ -135,6 +135,29 @@ static mig_status ctx_pano(mig_ctx *ctx, const Camera *ccam) {
     cam->d_pano_dir = d;
     cam->d_pano_row = r;
     return MIG_OK;
+}
+
+void set_pano_params(LevelParams &p, const Camera *cam, int32_t *pcnt) {
+    p.pano_A = cam->pano_A;
+    p.pano_Wc = cam->pano_Wc;
+    p.pano_step = cam->pano_step;
+    p.pano_bc = (const int2 *)cam->d_pano_bc;
+    p.pano_dir = (const int4 *)cam->d_pano_dir;
+    p.pano_row = (const int4 *)cam->d_pano_row;
+    p.pano_cnt = pcnt;
+}
+
+void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int count_cap, cudaStream_t s) {
+    const int items = Ld * p.K * p.tiles;
+    if (p.mode == MIG_MODE_INTERVAL) {
+        launch_count_interval(p, std::max(1, std::min((items + 7) / 8, ctx->num_sms * ctx->interval_ctas)), s);
+    } else if (p.mode == MIG_MODE_PANORAMIC) {
+        const int pitems = Ld * p.pano_A;
+        launch_pano_count(p, std::max(1, std::min((pitems + 7) / 8, ctx->num_sms * ctx->pano_ctas)), s);
+        launch_pano_window(p, std::max(1, std::min((Ld * p.K + 255) / 256, 1024)), s);
+    } else {
+        launch_count(p, std::max(1, std::min((items + 7) / 8, count_cap)), s);
+    }
 }
 
 void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a) {
@@ -531,15 +554,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = mode;
     p.max_anc = std::max(1, plan.max_depth);
-    if (pano) {
-        p.pano_A = cam->pano_A;
-        p.pano_Wc = cam->pano_Wc;
-        p.pano_step = cam->pano_step;
-        p.pano_bc = (const int2 *)cam->d_pano_bc;
-        p.pano_dir = (const int4 *)cam->d_pano_dir;
-        p.pano_row = (const int4 *)cam->d_pano_row;
-        p.pano_cnt = (int32_t *)(dev + o_pcnt);
-    }
+    if (pano) set_pano_params(p, cam, (int32_t *)(dev + o_pcnt));
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
@@ -550,23 +565,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
         const int Ld = plan.level_off[d + 1] - plan.level_off[d];
-        const int items = Ld * K * p.tiles;
-        const int cgrid = std::max(1, std::min((items + 7) / 8, count_cap));
-        if (mode == MIG_MODE_INTERVAL) {
-            timed_launch(ctx, kProfCount, [&] {
-                launch_count_interval(p, std::max(1, std::min((items + 7) / 8, ctx->num_sms * ctx->interval_ctas)),
-                                      ctx->stream);
-            });
-        } else if (pano) {
-            const int pitems = Ld * cam->pano_A;
-            timed_launch(ctx, kProfCount, [&] {
-                launch_pano_count(p, std::max(1, std::min((pitems + 7) / 8, ctx->num_sms * ctx->pano_ctas)),
-                                  ctx->stream);
-                launch_pano_window(p, std::max(1, std::min((Ld * K + 255) / 256, 1024)), ctx->stream);
-            });
-        } else {
-            timed_launch(ctx, kProfCount, [&] { launch_count(p, cgrid, ctx->stream); });
-        }
+        timed_launch(ctx, kProfCount, [&] { launch_level_count(ctx, p, Ld, count_cap, ctx->stream); });
         timed_launch(ctx, kProfSelect,
                      [&] { launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), ctx->stream); });
         const int ritems = plan.level_int[d] * render_tiles(p.W, p.H);

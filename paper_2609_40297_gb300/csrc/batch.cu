@@ -536,7 +536,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
     const mig_tile_config tc = ctx->tiles;
     Carve cv;
     struct TreeOff {
-        size_t node, ar, anc, loff, lint, lnodes, cnt, work, sel, out, arena;
+        size_t node, ar, anc, loff, lint, lnodes, cnt, work, sel, out, arena, pcnt;
     };
     std::vector<TreeOff> to(T);
     for (int t = 0; t < T; ++t) {
@@ -560,6 +560,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
     for (int t = 0; t < T; ++t) {
         to[t].sel = cv.take(4 * (size_t)items[t].plan.n);
         to[t].arena = cv.take(4 * (size_t)std::max(1, items[t].plan.n_internal) * items[t].cam->W * items[t].cam->H);
+        to[t].pcnt = items[t].mode == MIG_MODE_PANORAMIC ? cv.take(8 * (size_t)items[t].plan.n * items[t].cam->pano_A) : 0;
     }
     char *dev = nullptr;
     mig_status st = ctx_workspace(ctx, cv.off, (void **)&dev);
@@ -609,6 +610,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.out_yaw = p.out_abs + 2 * (size_t)n;
         p.mode = it.mode;
         p.max_anc = std::max(1, pl.max_depth);
+        if (it.mode == MIG_MODE_PANORAMIC) set_pano_params(p, it.cam, (int32_t *)(dev + to[t].pcnt));
         lp[t] = p;
     }
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
@@ -644,8 +646,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
             for (int d = 0; d <= pl.max_depth; ++d) {
                 p.lvl = d;
                 const int Ld = pl.level_off[d + 1] - pl.level_off[d];
-                const int chunks = Ld * p.K * p.tiles;
-                launch_count(p, std::max(1, std::min((chunks + 7) / 8, count_cap)), s);
+                launch_level_count(ctx, p, Ld, count_cap, s);
                 launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), s);
                 if (pl.level_int[d] > 0) launch_render(p, std::min(pl.level_int[d] * rt, cap), s);
             }
@@ -745,7 +746,7 @@ extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_t
     for (int t = 0; t < n_trees; ++t) {
         const mig_tree_desc &d = trees[t];
         if (!d.map || d.map->ctx != ctx) return fail(MIG_EINVAL, "tree_eval_batch: tree " + std::to_string(t) + " has no map of this context");
-        if (d.mode < 0 || d.mode > 2) return fail(MIG_EINVAL, "tree_eval_batch: unknown mode");
+        if (d.mode < 0 || d.mode > MIG_MODE_PANORAMIC) return fail(MIG_EINVAL, "tree_eval_batch: unknown mode");
         if (d.n_nodes < 0) return fail(MIG_EINVAL, "tree_eval_batch: negative node count");
         if (d.n_nodes > 0 && (!d.abs_gain || !d.marg_gain || !d.best_yaw))
             return fail(MIG_EINVAL, "tree_eval_batch: output array is NULL");
@@ -772,11 +773,14 @@ extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_t
     if (items.empty()) return MIG_OK;
     std::lock_guard<std::mutex> lk(ctx->mu);
     MIG_CUDA_TRY(cudaSetDevice(ctx->device));
+    bool per_mode_kernels = false;  // the interval and panoramic modes run on the stream-chain engine
     for (auto &it : items) {
         mig_status st = ctx_camera(ctx, it.sensor, &it.cam);
         if (st != MIG_OK) return st;
+        if (it.mode == MIG_MODE_PANORAMIC && (st = ctx_pano(ctx, it.cam)) != MIG_OK) return st;
+        per_mode_kernels |= it.mode == MIG_MODE_INTERVAL || it.mode == MIG_MODE_PANORAMIC;
     }
-    if (ctx->tiles.engine == 1) return batch_run_streams(ctx, items);
+    if (ctx->tiles.engine == 1 || per_mode_kernels) return batch_run_streams(ctx, items);
     if ((int)items.size() <= kBatchMaxTrees) return batch_run(ctx, items);
     for (size_t s = 0; s < items.size(); s += kBatchMaxTrees) {  // one persistent launch per group
         std::vector<BatchItem> part(std::make_move_iterator(items.begin() + s),

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "kernels.h"
 #include "mig.h"
 
 namespace mig {
@@ -139,6 +140,13 @@ namespace mig {
 mig_status ctx_workspace(mig_ctx *ctx, size_t bytes, void **out);
 mig_status ctx_pinned(mig_ctx *ctx, size_t bytes, void **out);
 mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out);
+// The panoramic tables of a context camera, built and uploaded on first use (ctx->mu held).
+mig_status ctx_pano(mig_ctx *ctx, const Camera *cam);
+// Panoramic level parameters from the camera's tables; pcnt = n * A * 2 int32 of workspace.
+void set_pano_params(LevelParams &p, const Camera *cam, int32_t *pcnt);
+// One level's count pass for p.mode: the sample, interval or panoramic kernels (Ld = nodes of
+// the level). The panoramic mode also runs its window sums, so launch_select may follow.
+void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int count_cap, cudaStream_t s);
 // records an event pair around launch() on the context stream when profiling is on
 void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a);
 void prof_end(mig_ctx *ctx, int kind, cudaEvent_t a);

@@ -142,6 +142,8 @@ mig_status admit(mig_server *s, Request &r) {
     const size_t WH = (size_t)r.sensor.width * r.sensor.height;
     mig_status st = ctx_camera(ctx, r.sensor, &r.cam);
     if (st != MIG_OK) return st;
+    const bool pano = r.mode == MIG_MODE_PANORAMIC;
+    if (pano && (st = ctx_pano(ctx, r.cam)) != MIG_OK) return st;
     Carve cv;
     const size_t o_node = cv.take(16 * (size_t)n), o_ar = cv.take(8 * (size_t)n);
     const size_t o_anc = cv.take(4 * (size_t)std::max(1, pl.total_anc)), o_loff = cv.take(4 * (size_t)(L + 1));
@@ -151,6 +153,7 @@ mig_status admit(mig_server *s, Request &r) {
     const size_t zero_end = cv.off;
     const size_t o_out = cv.take(12 * (size_t)n), o_sel = cv.take(4 * (size_t)n);
     const size_t o_arena = cv.take(4 * (size_t)std::max(1, pl.n_internal) * WH);
+    const size_t o_pcnt = pano ? cv.take(8 * (size_t)n * r.cam->pano_A) : 0;
     r.dev_bytes = cv.off;
     r.dev = (char *)ctx->alloc.alloc(r.dev_bytes, ctx->stream);
     if (!r.dev) return fail(MIG_ENOMEM, "server: request allocation failed");
@@ -209,6 +212,7 @@ mig_status admit(mig_server *s, Request &r) {
     p.mode = r.mode;
     p.stats = nullptr;
     p.max_anc = std::max(1, pl.max_depth);
+    if (pano) set_pano_params(p, r.cam, (int32_t *)(r.dev + o_pcnt));
     r.level = 0;
     return MIG_OK;
 }
@@ -267,7 +271,7 @@ mig_status run_step(mig_server *s) {
         const HostPlan &pl = r.plan;
         const int d = r.level;
         const int Ld = pl.level_off[d + 1] - pl.level_off[d];
-        launch_count(p, std::max(1, std::min((Ld * p.K * p.tiles + 7) / 8, count_cap)), st);
+        launch_level_count(ctx, p, Ld, count_cap, st);
         launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), st);
         if (pl.level_int[d] > 0 && d < pl.max_depth) launch_render(p, std::min(pl.level_int[d] * render_tiles(p.W, p.H), cap), st);
     }
@@ -410,7 +414,9 @@ extern "C" mig_status mig_server_create(mig_ctx *ctx, size_t arena_budget_bytes,
 extern "C" mig_status mig_server_submit(mig_server *s, const mig_tree_desc *d, uint64_t *ticket) {
     if (!s || !d || !ticket) return fail(MIG_EINVAL, "server_submit: NULL argument");
     if (!d->map || d->map->ctx != s->ctx) return fail(MIG_EINVAL, "server_submit: map of another context");
-    if (d->mode < 0 || d->mode > 2) return fail(MIG_EINVAL, "server_submit: unknown mode");
+    if (d->mode < 0 || d->mode > MIG_MODE_PANORAMIC) return fail(MIG_EINVAL, "server_submit: unknown mode");
+    if (d->mode == MIG_MODE_PANORAMIC && d->sensor.pitch_deg != 0.0f)
+        return fail(MIG_EINVAL, "panoramic mode: the camera must be level (pitch 0)");
     if (d->n_nodes < 1) return fail(MIG_EINVAL, "server_submit: a request needs at least one node");
     if (!d->abs_gain || !d->marg_gain || !d->best_yaw) return fail(MIG_EINVAL, "server_submit: output array is NULL");
     mig_status st = sensor_check(d->sensor, d->map->voxel);

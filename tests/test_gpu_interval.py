@@ -99,14 +99,14 @@ def test_interval_paper_scale_sampled_bit_exact(ctx):
         assert np.array_equal(got[k][sel], ref[k][sel]), k
 
 
-def test_interval_mode_rejected_where_unsupported(ctx):
+def test_unknown_mode_rejected(ctx):
     p = synth.tiny()
     m = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
     try:
         with pytest.raises(mig.MigError) as e:
-            mig.tree_eval_batch(ctx, [(p.tree.parent, p.tree.pos, p.sensor)], [m], mode=MODE)
+            mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=5)
         assert e.value.status == mig.MIG_EINVAL
         with pytest.raises(mig.MigError):
-            mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=5)
+            mig.tree_eval_batch(ctx, [(p.tree.parent, p.tree.pos, p.sensor)], [m], mode=5)
     finally:
         m.close()

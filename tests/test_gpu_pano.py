@@ -81,8 +81,6 @@ def test_pano_mode_rejections(ctx):
         with pytest.raises(mig.MigError) as e:
             mig.tree_eval(m, p.tree.parent, p.tree.pos, pitched, mode=MODE)
         assert e.value.status == mig.MIG_EINVAL
-        with pytest.raises(mig.MigError):
-            mig.tree_eval_batch(ctx, [(p.tree.parent, p.tree.pos, p.sensor)], [m], mode=MODE)
         got = mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=MODE)  # the context still works
         assert got["abs"].sum() > 0
     finally:

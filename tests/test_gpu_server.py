@@ -129,3 +129,28 @@ def test_destroy_drains_pending_requests(ctx):
         assert np.array_equal(out["marg"], ref["marg"])
     for m in maps:
         m.close()
+
+
+def test_interval_and_panoramic_requests_in_the_mix(ctx):
+    """Requests of the interval and panoramic modes served beside marginal ones: each result equals
+    a lone evaluation in its mode."""
+    probs = [synth.random_small(80 + i, n_nodes=9 + 4 * i, max_depth=2 + i % 4, sensor=Sensor(90, 60, 16, 10, 2.0, 8, 0.0))
+             for i in range(6)]
+    modes = [mig.MODE_MARGINAL, mig.MODE_INTERVAL, mig.MODE_PANORAMIC] * 2
+    maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in probs]
+    srv = mig.Server(ctx, arena_budget_bytes=1 << 30, max_inflight=16)
+    try:
+        subs = [srv.submit(m, p.tree.parent, p.tree.pos, p.sensor, mode=md) for p, m, md in zip(probs, maps, modes)]
+        for t, _ in subs:
+            assert srv.poll(t, timeout_us=30_000_000)
+        for (t, out), p, m, md in zip(subs, probs, maps, modes):
+            ref = mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=md)
+            for k in ("abs", "marg", "yaw"):
+                assert np.array_equal(out[k], ref[k]), (p.name, md, k)
+        with pytest.raises(mig.MigError):  # panoramic needs a level camera
+            srv.submit(maps[0], probs[0].tree.parent, probs[0].tree.pos, Sensor(90, 60, 16, 10, 2.0, 8, 10.0),
+                       mode=mig.MODE_PANORAMIC)
+    finally:
+        srv.close()
+        for m in maps:
+            m.close()

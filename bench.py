@@ -193,6 +193,7 @@ def run_ours(args):
     import torch
 
     import paper_2609_40297_gb300 as mig
+    import synth
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -257,7 +258,8 @@ def run_ours(args):
     e2e_value = ws * rays_per_step * len(e2e_ms) / (e2e_total / 1e3)
     # ---- the gain modes side by side (Table 2's absolute vs marginal columns, and the paper's
     # screen-space interval overlap against voxel-centre samples), each through the public host-array
-    # call, outside the timed region: median of 3 after one warm-up
+    # call, outside the timed region: median of 3 after one warm-up (a mode slower than 2 s per call:
+    # that first call alone)
     modes, yaws = {}, {}
     if rank == 0 and not args.no_modes:
         for name, md in (("marginal_samples", mig.MODE_MARGINAL), ("marginal_intervals", mig.MODE_INTERVAL),
@@ -265,14 +267,17 @@ def run_ours(args):
                          ("panoramic", mig.MODE_PANORAMIC)):
             if md == mig.MODE_PANORAMIC and s.pitch_deg != 0:
                 continue
-            mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+            first_ms = (time.perf_counter() - t0) * 1e3
             ts = []
-            for _ in range(3):
+            for _ in range(3 if first_ms < 2000 else 0):  # slow modes: the first call alone
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
                 ts.append((time.perf_counter() - t0) * 1e3)
-            ms = float(np.median(ts))
+            ms = float(np.median(ts)) if ts else first_ms
             modes[name] = {"ms_per_replan": ms, "rays_per_s": rays_per_step / (ms / 1e3),
                            "marg_sum": int(g["marg"].sum()), "abs_sum": int(g["abs"].sum())}
             if md == mig.MODE_PANORAMIC:
@@ -314,6 +319,7 @@ def run_ours(args):
             "data": "synthetic (seeded; stands in for the paper's Gazebo worlds)",
             "config": {"workload": WORKLOAD_DESC[args.workload], "nodes": n, "yaw_bins": s.yaw_bins,
                        "rays_per_node_yaw": s.width * s.height, "max_depth": max_depth,
+                       "inputs_sha256_16": synth.sha256(prob.map.grid, prob.tree.parent, prob.tree.pos)[:16],
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
             "replans_per_s": ws * args.steps / (total_ms / 1e3),
             "nodes_per_s": ws * n * args.steps / (total_ms / 1e3),

@@ -270,8 +270,9 @@ static int count_visit(void *vctx, const int32_t v[3], uint8_t code, const i64 t
  *      w = 1 / Z, and clip the 2D segment to the buffer [0, W] x [0, H] (Liang-Barsky);
  *   4. walk the pixels of the clipped segment with a 2D DDA ("Woo 1987"). Each visited pixel
  *      holds one portion [s_in, s_out) of the segment parameter s; its depth sample is taken
- *      at the portion's midpoint with w linear in s (Eq. 6), z = 1 / w, and the portion is
- *      observed iff z <= D_a[pixel] ("smaller or equal"). The maximal runs of observed
+ *      at the portion's midpoint with w linear in s (Eq. 6), and the portion is observed iff
+ *      its depth is <= D_a[pixel] ("smaller or equal"), compared in inverse depth as w D >= 1.
+ *      Boundary crossings use one reciprocal of the segment's screen extent. The maximal runs of observed
  *      portions are the intervals S_a of Eq. 7.
  * Then the 3D DDA counts (Sec. IV-B, last paragraph): an owned unknown voxel is a sample at
  * the midpoint of the ray's traversal of it (lambda_s, the exit capped at the range); it is
@@ -347,25 +348,28 @@ static int seg_setup(const cam_t *c, int ka, const i64 Pa[3], const i64 P[3], co
 /* step 4: the 2D DDA over the clipped segment; writes the portions in walk order */
 static int seg_walk(const seg2d_t *g, int W, int H, const uint32_t *D, portion_t *out) {
     float du = g->ub - g->ua, dv = g->vb - g->va;
+    /* boundary crossings: (boundary - start) times the reciprocal of the segment's extent */
+    float ru = du != 0.0f ? 1.0f / du : 0.0f, rv = dv != 0.0f ? 1.0f / dv : 0.0f;
     float s = g->s0;
     /* start pixel, clamped to the buffer in float (before any conversion to int) */
     float fi = floorf(g->ua + s * du), fj = floorf(g->va + s * dv);
     int i = fi < 0.0f ? 0 : (fi > (float)(W - 1) ? W - 1 : (int)fi);
     int j = fj < 0.0f ? 0 : (fj > (float)(H - 1) ? H - 1 : (int)fj);
     int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
-    float sx = si ? ((float)(si > 0 ? i + 1 : i) - g->ua) / du : INFINITY;
-    float sy = sj ? ((float)(sj > 0 ? j + 1 : j) - g->va) / dv : INFINITY;
+    float sx = si ? ((float)(si > 0 ? i + 1 : i) - g->ua) * ru : INFINITY;
+    float sy = sj ? ((float)(sj > 0 ? j + 1 : j) - g->va) * rv : INFINITY;
     int np = 0;
     for (;;) {
         float se = sx < sy ? sx : sy;
         if (g->s1 < se) se = g->s1;
         float sm = MUT(14) ? s : (s + se) * 0.5f;  /* Eq. 6 at the portion's midpoint */
         float wm = g->wa + sm * (g->wb - g->wa);
-        float zm = 1.0f / wm;
         float Dv = (float)D[(size_t)j * W + i] * (1.0f / 65536.0f);
+        /* z <= D ("smaller or equal"), compared in inverse depth: w D >= 1 */
+        float wD = wm * Dv;
         out[np].s_in = s;
         out[np].s_out = se;
-        out[np].obs = MUT(16) ? zm < Dv : zm <= Dv;
+        out[np].obs = MUT(16) ? wD > 1.0f : wD >= 1.0f;
         out[np].i = i;
         out[np].j = j;
         np++;
@@ -373,11 +377,11 @@ static int seg_walk(const seg2d_t *g, int W, int H, const uint32_t *D, portion_t
         if (sx <= sy) {
             i += si;
             if (i < 0 || i >= W) break;
-            sx = ((float)(si > 0 ? i + 1 : i) - g->ua) / du;
+            sx = ((float)(si > 0 ? i + 1 : i) - g->ua) * ru;
         } else {
             j += sj;
             if (j < 0 || j >= H) break;
-            sy = ((float)(sj > 0 ? j + 1 : j) - g->va) / dv;
+            sy = ((float)(sj > 0 ? j + 1 : j) - g->va) * rv;
         }
         s = se;
     }

@@ -10,7 +10,8 @@
 //   3. projected (Eq. 5) and clipped to the buffer [0, W] x [0, H] (Liang-Barsky);
 //   4. walked pixel by pixel (2D DDA); each visited pixel holds one portion of the segment, whose
 //      depth sample at the portion's midpoint (inverse depth linear in the screen parameter,
-//      Eq. 6) is compared with the stored depth, "smaller or equal" => observed.
+//      Eq. 6) is compared with the stored depth, "smaller or equal" => observed, in inverse depth
+//      (w D >= 1); boundary crossings use one reciprocal of the segment's screen extent.
 // A sample belongs to the first portion, in walk order, that contains its perspective-correct
 // screen parameter. Every floating-point step is one correctly rounded single-precision
 // operation (__fadd_rn and friends: no contraction), in a fixed order, so the counts are
@@ -160,22 +161,24 @@ __device__ __forceinline__ float sample_lambda(uint32_t ne, uint32_t ade, uint32
 __device__ uint32_t seg_walk(const Seg &g, int W, int H, const uint32_t *D, const float *sv, int stride, uint32_t cand,
                              uint32_t &pend) {
     const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
+    // boundary crossings: (boundary - start) times the reciprocal of the segment's extent
+    const float ru = du != 0.0f ? fdiv(1.0f, du) : 0.0f, rv = dv != 0.0f ? fdiv(1.0f, dv) : 0.0f;
     float s = g.s0;
     const float fi = floorf(fadd(g.ua, fmul(s, du))), fj = floorf(fadd(g.va, fmul(s, dv)));
     int i = fi < 0.0f ? 0 : (fi > __int2float_rn(W - 1) ? W - 1 : __float2int_rz(fi));
     int j = fj < 0.0f ? 0 : (fj > __int2float_rn(H - 1) ? H - 1 : __float2int_rz(fj));
     const int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
-    float sx = si ? fdiv(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), du) : __int_as_float(0x7f800000);
-    float sy = sj ? fdiv(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), dv) : __int_as_float(0x7f800000);
+    float sx = si ? fmul(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), ru) : __int_as_float(0x7f800000);
+    float sy = sj ? fmul(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), rv) : __int_as_float(0x7f800000);
     uint32_t walked = 0;
     for (;;) {
         float se = sx < sy ? sx : sy;
         if (g.s1 < se) se = g.s1;
         ++walked;
         const float sm = fmul(fadd(s, se), 0.5f);
-        const float zm = fdiv(1.0f, fadd(g.wa, fmul(sm, fsub(g.wb, g.wa))));
+        const float wm = fadd(g.wa, fmul(sm, fsub(g.wb, g.wa)));
         const float Dv = fmul(__uint2float_rn(__ldg(D + (size_t)j * W + i)), 1.52587890625e-05f);
-        const bool obs = zm <= Dv;
+        const bool obs = fmul(wm, Dv) >= 1.0f;  // z <= D in inverse depth
         for (uint32_t c = cand; c; c &= c - 1) {
             const int q = __ffs(c) - 1;
             const float x = sv[q * stride];
@@ -188,11 +191,11 @@ __device__ uint32_t seg_walk(const Seg &g, int W, int H, const uint32_t *D, cons
         if (sx <= sy) {
             i += si;
             if (i < 0 || i >= W) break;
-            sx = fdiv(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), du);
+            sx = fmul(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), ru);
         } else {
             j += sj;
             if (j < 0 || j >= H) break;
-            sy = fdiv(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), dv);
+            sy = fmul(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), rv);
         }
         s = se;
     }

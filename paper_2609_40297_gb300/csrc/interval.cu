@@ -17,10 +17,15 @@
 // operation (__fadd_rn and friends: no contraction), in a fixed order, so the counts are
 // reproducible bit for bit.
 //
+// The walk is not stepped pixel by pixel here: its portion boundaries are a fixed function of the
+// boundary index (the same rounded operations as the walk), non-decreasing along it, so the
+// portion that contains a sample is found directly by counting the column and row crossings at or
+// before the sample's screen parameter (seg_lookup). The result is the walk's, bit for bit.
+//
 // Layout: one warp per work item (node, yaw, tile of rays), taken from the level's atomic work
-// counter; each lane casts rays lane, lane + 32, ... of the tile. A lane keeps up to kIvChunk
-// pending samples (ray fractions) in shared memory and runs the ancestors' interval walks over
-// them when the buffer fills or the ray ends, so the walks are paid only by rays with samples.
+// counter; a lane takes the tile's next ray as soon as its ray ends. Owned samples (ray fraction,
+// pixel) go to a per-warp queue; each full batch of 32 is tested against the ancestors with one
+// sample per lane.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +44,6 @@ using namespace dev;
 
 constexpr int kIvWarps = 8;
 constexpr int kIvThreads = kIvWarps * 32;
-constexpr int kIvChunk = 16;  // pending samples per lane
 constexpr float kZNear = 1.0f / 1024.0f;  // near end of the valid depth range, voxel units
 
 // an ancestor as the interval walk needs it: position (Q16), selected yaw, depth buffer
@@ -155,96 +159,91 @@ __device__ __forceinline__ float sample_lambda(uint32_t ne, uint32_t ade, uint32
     return fmul(fadd(lin, lout), 0.5f);
 }
 
-// step 4 for the samples in `cand` (bit q = pending sample q, screen parameter sv[q * stride]):
-// walks the portions in order; each sample is decided by the first portion containing it and
-// removed from `pend` when that portion is observed. Returns the portions walked.
-__device__ uint32_t seg_walk(const Seg &g, int W, int H, const uint32_t *D, const float *sv, int stride, uint32_t cand,
-                             uint32_t &pend) {
-    const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
-    // boundary crossings: (boundary - start) times the reciprocal of the segment's extent
-    const float ru = du != 0.0f ? fdiv(1.0f, du) : 0.0f, rv = dv != 0.0f ? fdiv(1.0f, dv) : 0.0f;
-    float s = g.s0;
-    const float fi = floorf(fadd(g.ua, fmul(s, du))), fj = floorf(fadd(g.va, fmul(s, dv)));
-    int i = fi < 0.0f ? 0 : (fi > __int2float_rn(W - 1) ? W - 1 : __float2int_rz(fi));
-    int j = fj < 0.0f ? 0 : (fj > __int2float_rn(H - 1) ? H - 1 : __float2int_rz(fj));
-    const int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
-    float sx = si ? fmul(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), ru) : __int_as_float(0x7f800000);
-    float sy = sj ? fmul(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), rv) : __int_as_float(0x7f800000);
-    uint32_t walked = 0;
-    for (;;) {
-        float se = sx < sy ? sx : sy;
-        if (g.s1 < se) se = g.s1;
-        ++walked;
-        const float sm = fmul(fadd(s, se), 0.5f);
-        const float wm = fadd(g.wa, fmul(sm, fsub(g.wb, g.wa)));
-        const float Dv = fmul(__uint2float_rn(__ldg(D + (size_t)j * W + i)), 1.52587890625e-05f);
-        const bool obs = fmul(wm, Dv) >= 1.0f;  // z <= D in inverse depth
-        for (uint32_t c = cand; c; c &= c - 1) {
-            const int q = __ffs(c) - 1;
-            const float x = sv[q * stride];
-            if (s <= x && x < se) {
-                cand &= ~(1u << q);
-                if (obs) pend &= ~(1u << q);
-            }
-        }
-        if (!cand || !(se < g.s1)) break;
-        if (sx <= sy) {
-            i += si;
-            if (i < 0 || i >= W) break;
-            sx = fmul(fsub(__int2float_rn(si > 0 ? i + 1 : i), g.ua), ru);
-        } else {
-            j += sj;
-            if (j < 0 || j >= H) break;
-            sy = fmul(fsub(__int2float_rn(sj > 0 ? j + 1 : j), g.va), rv);
-        }
-        s = se;
-    }
-    return walked;
+// Column (or row) crossings of the walk: boundary b_k = b0 + sgn k is crossed at screen parameter
+// x(k) = (b_k - a0) * r, the walk's own formula, non-decreasing in k. Counts the crossings at or
+// before s among k < kmax (crossing kmax leaves the buffer); lo / hi = the last crossing at or
+// before s and the next one. The count starts from a float estimate and is corrected exactly.
+__device__ __forceinline__ int count_crossings(float a0, float r, float d, int b0, int sgn, int kmax, float s,
+                                               float &lo, float &hi) {
+    const float est = (float)sgn * (s * d + a0 - (float)b0) + 1.0f;  // estimate only; corrected below
+    int k = !(est > 0.0f) ? 0 : (est >= (float)kmax ? kmax : (int)est);
+    auto x = [&](int kk) { return fmul(fsub(__int2float_rn(b0 + sgn * kk), a0), r); };
+    while (k > 0 && x(k - 1) > s) --k;
+    while (k < kmax && x(k) <= s) ++k;
+    lo = k > 0 ? x(k - 1) : __int_as_float(0xff800000);
+    hi = k < kmax ? x(k) : __int_as_float(0x7f800000);
+    return k;
 }
 
-// Exclusion of a lane's pending samples (ray fractions lam[q * stride], q < ns): the union over
-// the ancestors (parent first) of their observed portions. Returns the samples left (marginal).
+// Step 4 for one screen parameter s in [s0, s1): the walk's portion containing s, found directly.
+// The walk crosses column and row boundaries in the order of their crossing parameters, so at s
+// it is in column i0 + si * (column crossings <= s) and row j0 + sj * (row crossings <= s), in the
+// portion from the latest crossing at or before s (s0 if none) to the next one (capped at s1).
+// True if that portion is observed; false if not, or if the walk leaves the buffer before s.
+__device__ bool seg_lookup(const Seg &g, int W, int H, const uint32_t *D, float s) {
+    const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
+    const float ru = du != 0.0f ? fdiv(1.0f, du) : 0.0f, rv = dv != 0.0f ? fdiv(1.0f, dv) : 0.0f;
+    const float fi = floorf(fadd(g.ua, fmul(g.s0, du))), fj = floorf(fadd(g.va, fmul(g.s0, dv)));
+    const int i0 = fi < 0.0f ? 0 : (fi > __int2float_rn(W - 1) ? W - 1 : __float2int_rz(fi));
+    const int j0 = fj < 0.0f ? 0 : (fj > __int2float_rn(H - 1) ? H - 1 : __float2int_rz(fj));
+    const int si = du > 0.0f ? 1 : (du < 0.0f ? -1 : 0), sj = dv > 0.0f ? 1 : (dv < 0.0f ? -1 : 0);
+    float xlo = __int_as_float(0xff800000), xhi = __int_as_float(0x7f800000), ylo = xlo, yhi = xhi;
+    int nx = 0, ny = 0;
+    if (si) {
+        const int kmax = si > 0 ? W - i0 : i0 + 1;
+        nx = count_crossings(g.ua, ru, du, si > 0 ? i0 + 1 : i0, si, kmax, s, xlo, xhi);
+        if (nx == kmax) return false;
+    }
+    if (sj) {
+        const int kmax = sj > 0 ? H - j0 : j0 + 1;
+        ny = count_crossings(g.va, rv, dv, sj > 0 ? j0 + 1 : j0, sj, kmax, s, ylo, yhi);
+        if (ny == kmax) return false;
+    }
+    const int i = i0 + si * nx, j = j0 + sj * ny;
+    const float s_in = (nx == 0 && ny == 0) ? g.s0 : (xlo > ylo ? xlo : ylo);
+    float s_out = xhi < yhi ? xhi : yhi;
+    if (g.s1 < s_out) s_out = g.s1;
+    const float sm = fmul(fadd(s_in, s_out), 0.5f);
+    const float wm = fadd(g.wa, fmul(sm, fsub(g.wb, g.wa)));
+    const float Dv = fmul(__uint2float_rn(__ldg(D + (size_t)j * W + i)), 1.52587890625e-05f);
+    return fmul(wm, Dv) >= 1.0f;  // z <= D in inverse depth
+}
+
+// Is the sample (ray fraction lam of the ray through pixel pix, yaw ck / sk, origin P) inside an
+// ancestor's observed portions? Ancestors parent first; the ray's set-up is rebuilt per sample.
 template <bool STATS>
-__device__ int flush_samples(const LevelParams &p, const IvAnc *anc, int na, const int64_t P[3], const int64_t E[3],
-                             float zf, const float *lam, float *sv, int stride, int ns, unsigned long long &st_seg,
-                             unsigned long long &st_por) {
-    uint32_t pend = ns >= 32 ? 0xffffffffu : ((1u << ns) - 1u);
-    for (int a = 0; a < na && pend; ++a) {
+__device__ bool iv_observed(const LevelParams &p, const IvAnc *anc, int na, const int64_t P[3], int ck, int sk,
+                            float zf, float lam, int pix, uint32_t &st_seg) {
+    const int4 b = p.body[pix];
+    int dx, dy, dz;
+    ray_dir(b, ck, sk, dx, dy, dz);
+    const int64_t E[3] = {P[0] + (((int64_t)p.Tq * dx) >> 30), P[1] + (((int64_t)p.Tq * dy) >> 30),
+                          P[2] + (((int64_t)p.Tq * dz) >> 30)};
+    for (int a = 0; a < na; ++a) {
         const IvAnc &A = anc[a];
         Seg g;
         if constexpr (STATS) ++st_seg;
         if (!seg_setup(p.yawtab + A.yaw * 12 + 2, make_int3(A.px, A.py, A.pz), P, E, zf, p.W, p.H, g)) continue;
-        uint32_t cand = 0;
-        for (uint32_t c = pend; c; c &= c - 1) {
-            const int q = __ffs(c) - 1;
-            float s;
-            if (seg_param(g, lam[q * stride], s)) {
-                sv[q * stride] = s;
-                cand |= 1u << q;
-            }
-        }
-        if (!cand) continue;
-        const uint32_t w = seg_walk(g, p.W, p.H, A.D, sv, stride, cand, pend);
-        if constexpr (STATS) st_por += w;
+        float s;
+        if (seg_param(g, lam, s) && seg_lookup(g, p.W, p.H, A.D, s)) return true;
     }
-    return __popc(pend);
+    return false;
 }
 
 template <bool STATS>
 __global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const LevelParams p) {
     extern __shared__ IvAnc s_iv_anc[];
-    __shared__ float s_lam[kIvChunk][kIvThreads];
-    __shared__ float s_sv[kIvChunk][kIvThreads];
+    __shared__ unsigned long long s_q[kIvWarps][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     IvAnc *anc = s_iv_anc + warp * p.max_anc;
-    float *lam = &s_lam[0][threadIdx.x];
-    float *sv = &s_sv[0][threadIdx.x];
+    unsigned long long *q = s_q[warp];
     const int l0 = p.level_off[p.lvl];
     const int L = p.level_off[p.lvl + 1] - l0;
     const int items = L * p.K * p.tiles;
     const float zf = fmul(__ll2float_rn(p.Tq), 1.52587890625e-05f);   // range, voxel units
     const float T = fmul(__ll2float_rn(p.Tq), 9.313225746154785e-10f);  // range, crossing units
-    unsigned long long st_rays = 0, st_steps = 0, st_unk = 0, st_seg = 0, st_por = 0;
+    uint32_t st_rays = 0, st_steps = 0, st_unk = 0, st_seg = 0;
     for (;;) {
         int c = 0;
         if (lane == 0) c = atomicAdd(p.work + p.lvl, 1);
@@ -260,13 +259,13 @@ __global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const Lev
         for (int t = lane; t < na; t += 32) {
             const int a = p.anc[ar.x + t];
             const int4 an = p.node[a];
-            IvAnc r;
-            r.px = an.x;
-            r.py = an.y;
-            r.pz = an.z;
-            r.yaw = p.sel_yaw[a];
-            r.D = p.arena + (size_t)an.w * p.W * p.H;
-            anc[t] = r;
+            IvAnc rec;
+            rec.px = an.x;
+            rec.py = an.y;
+            rec.pz = an.z;
+            rec.yaw = p.sel_yaw[a];
+            rec.D = p.arena + (size_t)an.w * p.W * p.H;
+            anc[t] = rec;
         }
         __syncwarp();
         const int32_t *yk = p.yawtab + k * 12;
@@ -274,51 +273,89 @@ __global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const Lev
         const int64_t P[3] = {nd.x, nd.y, nd.z};
         const int tx0 = (tile % p.tiles_x) * p.tile_w, ty0 = (tile / p.tiles_x) * p.tile_h;
         const int tile_rays = p.tile_w * p.tile_h;
-        int c_abs = 0, c_mrg = 0;
-        for (int idx = lane; idx < tile_rays; idx += 32) {
-            const int ti = tx0 + idx % p.tile_w, tj = ty0 + idx / p.tile_w;
-            if (ti >= p.W || tj >= p.H) continue;
-            const int4 b = p.body[tj * p.W + ti];
-            int dx, dy, dz;
-            ray_dir(b, ck, sk, dx, dy, dz);
-            const int64_t E[3] = {P[0] + (((int64_t)p.Tq * dx) >> 30), P[1] + (((int64_t)p.Tq * dy) >> 30),
-                                  P[2] + (((int64_t)p.Tq * dz) >> 30)};
-            RayIn r;
-            ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
-            if constexpr (STATS) ++st_rays;
-            uint32_t ne = 0, ade = 1;
-            int ns = 0;
-            for (;;) {
-                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
-                if constexpr (STATS) ++st_steps;
-                if (code == kOcc) break;
-                uint32_t nx = 0, adx = 1;
-                bool owned = false;
-                if (code == kUnknown) {
-                    if constexpr (STATS) ++st_unk;
-                    // owner test (reading A1): the voxel centre projects into pixel (ti, tj)
-                    const int rx = voxel_offset(r.nx, r.sx), ry = voxel_offset(r.ny, r.sy),
-                              rz = voxel_offset(r.nz, r.sz);
-                    const int64_t Z = (int64_t)yk[8] * rx + (int64_t)yk[9] * ry + (int64_t)yk[10] * rz;
-                    const int64_t U = (int64_t)yk[2] * rx + (int64_t)yk[3] * ry + (int64_t)yk[4] * rz;
-                    const int64_t V = (int64_t)yk[5] * rx + (int64_t)yk[6] * ry + (int64_t)yk[7] * rz;
-                    const int64_t iZ = (int64_t)ti * Z, jZ = (int64_t)tj * Z;
-                    owned = Z > 0 && U >= iZ && U < iZ + Z && V >= jZ && V < jZ + Z;
-                }
-                const bool more = ray_step<true>(r, nx, adx);  // nx / adx: this voxel's exit crossing
-                if (owned) {
-                    ++c_abs;
-                    lam[ns * kIvThreads] = sample_lambda(ne, ade, nx, adx, T);
-                    if (++ns == kIvChunk) {
-                        c_mrg += flush_samples<STATS>(p, anc, na, P, E, zf, lam, sv, kIvThreads, ns, st_seg, st_por);
-                        ns = 0;
+        int next = 0, ti = 0, tj = 0, qn = 0, c_abs = 0, c_mrg = 0;
+        bool have = false;
+        RayIn r;
+        uint32_t ne = 0, ade = 1;
+        for (;;) {
+            // lanes without a ray take the tile's next rays in order
+            const unsigned need = __ballot_sync(0xffffffffu, !have);
+            if (need && next < tile_rays) {
+                const int idx = next + __popc(need & lt_mask);
+                next += __popc(need);
+                if (!have && idx < tile_rays) {
+                    ti = tx0 + idx % p.tile_w;
+                    tj = ty0 + idx / p.tile_w;
+                    if (ti < p.W && tj < p.H) {
+                        const int4 b = p.body[tj * p.W + ti];
+                        int dx, dy, dz;
+                        ray_dir(b, ck, sk, dx, dy, dz);
+                        ray_init(r, p.grid, nd.x, nd.y, nd.z, dx, dy, dz, p.Tq);
+                        ne = 0;
+                        ade = 1;
+                        have = true;
+                        if constexpr (STATS) ++st_rays;
                     }
                 }
-                if (!more) break;
-                ne = nx;
-                ade = adx;
             }
-            if (ns) c_mrg += flush_samples<STATS>(p, anc, na, P, E, zf, lam, sv, kIvThreads, ns, st_seg, st_por);
+            if (!__any_sync(0xffffffffu, have)) {
+                if (next >= tile_rays) break;
+                continue;
+            }
+            bool owned = false;
+            unsigned long long key = 0;
+            if (have) {
+                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+                if constexpr (STATS) ++st_steps;
+                if (code == kOcc) {
+                    have = false;
+                } else {
+                    if (code == kUnknown) {
+                        if constexpr (STATS) ++st_unk;
+                        // owner test (reading A1): the voxel centre projects into pixel (ti, tj)
+                        const int rx = voxel_offset(r.nx, r.sx), ry = voxel_offset(r.ny, r.sy),
+                                  rz = voxel_offset(r.nz, r.sz);
+                        const int64_t Z = (int64_t)yk[8] * rx + (int64_t)yk[9] * ry + (int64_t)yk[10] * rz;
+                        const int64_t U = (int64_t)yk[2] * rx + (int64_t)yk[3] * ry + (int64_t)yk[4] * rz;
+                        const int64_t iZ = (int64_t)ti * Z;
+                        if (Z > 0 && U >= iZ && U < iZ + Z) {
+                            const int64_t V = (int64_t)yk[5] * rx + (int64_t)yk[6] * ry + (int64_t)yk[7] * rz;
+                            const int64_t jZ = (int64_t)tj * Z;
+                            owned = V >= jZ && V < jZ + Z;
+                        }
+                    }
+                    uint32_t nx = 0, adx = 1;
+                    const bool more = ray_step<true>(r, nx, adx);  // nx / adx: this voxel's exit crossing
+                    if (owned)
+                        key = (unsigned long long)__float_as_uint(sample_lambda(ne, ade, nx, adx, T)) |
+                              ((unsigned long long)(uint32_t)(tj * p.W + ti) << 32);
+                    ne = nx;
+                    ade = adx;
+                    have = more;
+                }
+            }
+            c_abs += owned;
+            const unsigned bal = __ballot_sync(0xffffffffu, owned);
+            if (bal) {
+                if (owned) q[qn + __popc(bal & lt_mask)] = key;
+                qn += __popc(bal);
+                if (qn >= 32) {  // a full batch: every lane tests one sample against the ancestors
+                    __syncwarp();
+                    const unsigned long long e = q[lane];
+                    c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, __uint_as_float((uint32_t)e),
+                                                 (int)(e >> 32), st_seg);
+                    __syncwarp();
+                    if (lane < qn - 32) q[lane] = q[lane + 32];
+                    __syncwarp();
+                    qn -= 32;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < qn) {
+            const unsigned long long e = q[lane];
+            c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, __uint_as_float((uint32_t)e), (int)(e >> 32),
+                                         st_seg);
         }
         c_abs = __reduce_add_sync(0xffffffffu, c_abs);
         c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);
@@ -329,13 +366,19 @@ __global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const Lev
         if constexpr (STATS) {
             if (lane == 0) atomicAdd(p.stats + 3, (unsigned long long)(uint32_t)c_abs);
         }
+        __syncwarp();
     }
     if constexpr (STATS) {
-        atomicAdd(p.stats + 0, st_rays);
-        atomicAdd(p.stats + 1, st_steps);
-        atomicAdd(p.stats + 2, st_unk);
-        atomicAdd(p.stats + 4, st_seg);
-        atomicAdd(p.stats + 5, st_por);
+        st_rays = __reduce_add_sync(0xffffffffu, st_rays);
+        st_steps = __reduce_add_sync(0xffffffffu, st_steps);
+        st_unk = __reduce_add_sync(0xffffffffu, st_unk);
+        st_seg = __reduce_add_sync(0xffffffffu, st_seg);
+        if (lane == 0) {
+            atomicAdd(p.stats + 0, (unsigned long long)st_rays);
+            atomicAdd(p.stats + 1, (unsigned long long)st_steps);
+            atomicAdd(p.stats + 2, (unsigned long long)st_unk);
+            atomicAdd(p.stats + 4, (unsigned long long)st_seg);
+        }
     }
 }
 

@@ -290,6 +290,7 @@ typedef struct {
     float ua, va, ub, vb; /* projected clipped endpoints (pixels) */
     float wa, wb;         /* inverse depths at the endpoints */
     float s0, s1;         /* Liang-Barsky range of s over [0, 1] */
+    float ru, rv;         /* reciprocals of the segment's screen extent (0 when it is 0) */
 } seg2d_t;
 
 typedef struct {
@@ -327,16 +328,21 @@ static int seg_setup(const cam_t *c, int ka, const i64 Pa[3], const i64 P[3], co
     float Ub = U0 + hi * dU, Vb = V0 + hi * dV, Zb = Z0 + hi * dZ;
     if (!(Za > 0.0f && Zb > 0.0f)) return 0;
     g->lo = lo; g->hi = hi; g->Za = Za; g->Zb = Zb;
-    g->ua = Ua / Za; g->va = Va / Za; g->ub = Ub / Zb; g->vb = Vb / Zb;
+    /* Eq. 5 with the inverse depths of Eq. 6: u = U w, v = V w */
     g->wa = 1.0f / Za; g->wb = 1.0f / Zb;
-    /* Liang-Barsky ("Liang 1984") against 0 <= u <= W, 0 <= v <= H */
+    g->ua = Ua * g->wa; g->va = Va * g->wa; g->ub = Ub * g->wb; g->vb = Vb * g->wb;
+    /* Liang-Barsky ("Liang 1984") against 0 <= u <= W, 0 <= v <= H; each edge's crossing is
+     * q times the reciprocal of p (+-1/du or +-1/dv) */
     float du = g->ub - g->ua, dv = g->vb - g->va;
+    g->ru = du != 0.0f ? 1.0f / du : 0.0f;
+    g->rv = dv != 0.0f ? 1.0f / dv : 0.0f;
     float p[4] = {-du, du, -dv, dv};
+    float rp[4] = {-g->ru, g->ru, -g->rv, g->rv};
     float q[4] = {g->ua, (float)c->W - g->ua, g->va, (float)c->H - g->va};
     float s0 = 0.0f, s1 = 1.0f;
     for (int e = 0; e < 4; ++e) {
         if (p[e] == 0.0f) { if (q[e] < 0.0f) return 0; continue; }
-        float r = q[e] / p[e];
+        float r = q[e] * rp[e];
         if (p[e] < 0.0f) { if (r > s1) return 0; if (r > s0) s0 = r; }
         else { if (r < s0) return 0; if (r < s1) s1 = r; }
     }
@@ -349,7 +355,7 @@ static int seg_setup(const cam_t *c, int ka, const i64 Pa[3], const i64 P[3], co
 static int seg_walk(const seg2d_t *g, int W, int H, const uint32_t *D, portion_t *out) {
     float du = g->ub - g->ua, dv = g->vb - g->va;
     /* boundary crossings: (boundary - start) times the reciprocal of the segment's extent */
-    float ru = du != 0.0f ? 1.0f / du : 0.0f, rv = dv != 0.0f ? 1.0f / dv : 0.0f;
+    float ru = g->ru, rv = g->rv;
     float s = g->s0;
     /* start pixel, clamped to the buffer in float (before any conversion to int) */
     float fi = floorf(g->ua + s * du), fj = floorf(g->va + s * dv);

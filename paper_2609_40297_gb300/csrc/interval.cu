@@ -58,6 +58,7 @@ struct Seg {
     float ua, va, ub, vb;  // projected clipped endpoints (pixels)
     float wa, wb;          // inverse depths at the endpoints
     float s0, s1;          // Liang-Barsky range of the screen parameter
+    float ru, rv;          // reciprocals of the segment's screen extent (0 when it is 0)
 };
 
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
@@ -108,15 +109,20 @@ __device__ bool seg_setup(const int32_t *m, const int3 Pa, const int64_t P[3], c
     g.hi = hi;
     g.Za = Za;
     g.Zb = Zb;
-    g.ua = fdiv(Ua, Za);
-    g.va = fdiv(Va, Za);
-    g.ub = fdiv(Ub, Zb);
-    g.vb = fdiv(Vb, Zb);
+    // Eq. 5 with the inverse depths of Eq. 6: u = U w, v = V w
     g.wa = fdiv(1.0f, Za);
     g.wb = fdiv(1.0f, Zb);
-    // Liang-Barsky against 0 <= u <= W, 0 <= v <= H (edges in the order -u, +u, -v, +v)
+    g.ua = fmul(Ua, g.wa);
+    g.va = fmul(Va, g.wa);
+    g.ub = fmul(Ub, g.wb);
+    g.vb = fmul(Vb, g.wb);
+    // Liang-Barsky against 0 <= u <= W, 0 <= v <= H (edges in the order -u, +u, -v, +v); each
+    // edge's crossing is q times the reciprocal of p
     const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
+    g.ru = du != 0.0f ? fdiv(1.0f, du) : 0.0f;
+    g.rv = dv != 0.0f ? fdiv(1.0f, dv) : 0.0f;
     const float pe[4] = {-du, du, -dv, dv};
+    const float rp[4] = {-g.ru, g.ru, -g.rv, g.rv};
     const float qe[4] = {g.ua, fsub(__int2float_rn(W), g.ua), g.va, fsub(__int2float_rn(H), g.va)};
     float s0 = 0.0f, s1 = 1.0f;
 #pragma unroll
@@ -125,7 +131,7 @@ __device__ bool seg_setup(const int32_t *m, const int3 Pa, const int64_t P[3], c
             if (qe[e] < 0.0f) return false;
             continue;
         }
-        const float r = fdiv(qe[e], pe[e]);
+        const float r = fmul(qe[e], rp[e]);
         if (pe[e] < 0.0f) {
             if (r > s1) return false;
             if (r > s0) s0 = r;
@@ -182,7 +188,7 @@ __device__ __forceinline__ int count_crossings(float a0, float r, float d, int b
 // True if that portion is observed; false if not, or if the walk leaves the buffer before s.
 __device__ bool seg_lookup(const Seg &g, int W, int H, const uint32_t *D, float s) {
     const float du = fsub(g.ub, g.ua), dv = fsub(g.vb, g.va);
-    const float ru = du != 0.0f ? fdiv(1.0f, du) : 0.0f, rv = dv != 0.0f ? fdiv(1.0f, dv) : 0.0f;
+    const float ru = g.ru, rv = g.rv;
     const float fi = floorf(fadd(g.ua, fmul(g.s0, du))), fj = floorf(fadd(g.va, fmul(g.s0, dv)));
     const int i0 = fi < 0.0f ? 0 : (fi > __int2float_rn(W - 1) ? W - 1 : __float2int_rz(fi));
     const int j0 = fj < 0.0f ? 0 : (fj > __int2float_rn(H - 1) ? H - 1 : __float2int_rz(fj));

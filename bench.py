@@ -12,8 +12,10 @@ per step, no collective on the data path; value = all ranks' rays / max-over-ran
 
 --impl reference: the CPU oracle (the plain C restatement of the method) timed on this host's
 cores on a bounded sample of the same workload, same metric and unit.
---workload batched | serving | large | tiny: the other configurations (batched vs plain, the
-serving loop with p50/p99 latency); see the design doc.
+--workload batched | serving | large | tiny: the other configurations (64 trees batched against 64
+plain calls; the serving loop with p50/p99 latency; the 800x800x200 large workload; the tiny one).
+The single-tree workloads also time every gain mode through the public call (`modes`) and, from the
+oracle, report each mode's gap to the exact marginal gain.
 """
 from __future__ import annotations
 

@@ -42,6 +42,11 @@ namespace {
 
 using namespace dev;
 
+// minimum resident interval-kernel CTAs per SM requested from the register allocator
+#ifndef MIG_IV_MINB
+#define MIG_IV_MINB 4
+#endif
+
 constexpr int kIvWarps = 8;
 constexpr int kIvThreads = kIvWarps * 32;
 constexpr float kZNear = 1.0f / 1024.0f;  // near end of the valid depth range, voxel units
@@ -237,7 +242,7 @@ __device__ bool iv_observed(const LevelParams &p, const IvAnc *anc, int na, cons
 }
 
 template <bool STATS>
-__global__ void __launch_bounds__(kIvThreads, 2) interval_count_kernel(const LevelParams p) {
+__global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel(const LevelParams p) {
     extern __shared__ IvAnc s_iv_anc[];
     __shared__ unsigned long long s_q[kIvWarps][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -5,7 +5,6 @@ equality of gains, yaws, per-(node, yaw) counts and depth buffers."""
 import numpy as np
 import pytest
 
-import oracle
 import synth
 from synth import Sensor
 
@@ -73,30 +72,13 @@ def test_interval_deep_chain_and_unknown_map(ctx):
     assert_same(got, ref)
 
 
-def test_interval_paper_scale_sampled_bit_exact(ctx):
-    """The 500-node paper-scale workload, whole tree on the GPU in the interval mode, checked against
-    the oracle on every node of depth <= 2 and of two seeded root-to-leaf paths."""
+def test_interval_paper_scale_full_tree_bit_exact(ctx):
+    """The 500-node paper-scale workload in the interval mode, every node and yaw, against the
+    oracle's literal interval walk."""
     p = synth.paper_scale()
-    m = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
-    try:
-        got = mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, mode=MODE)
-    finally:
-        m.close()
-    parent, depth = p.tree.parent, p.tree.depth()
-    is_leaf = np.ones(p.tree.n, bool)
-    is_leaf[parent[parent >= 0]] = False
-    mask = (depth <= 2).astype(np.uint8)
-    rng = np.random.default_rng(2020)
-    for leaf in rng.choice(np.nonzero(is_leaf & (depth >= depth.max() - 1))[0], size=2, replace=False):
-        q = int(leaf)
-        while q >= 0:
-            mask[q] = 1
-            q = int(parent[q])
-    ref = oracle.eval_tree(p.map.grid, p.map.voxel_size, p.map.origin, parent, p.tree.pos, p.sensor, mode=MODE,
-                           node_mask=mask)
-    sel = mask.astype(bool)
-    for k in ("abs", "marg", "yaw"):
-        assert np.array_equal(got[k][sel], ref[k][sel]), k
+    got, ref = run_both(ctx, p.map.grid, p.map.voxel_size, p.map.origin, p.tree.parent, p.tree.pos, p.sensor,
+                        mode=MODE, depth=False)
+    assert_same(got, ref, ("abs", "marg", "yaw", "cnt_abs", "cnt_marg"))
 
 
 def test_unknown_mode_rejected(ctx):

@@ -369,11 +369,20 @@ def run_batched(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    n_trees = int(os.environ.get("MIG_BATCH_TREES", "64"))
-    probs = synth.batched(seed_base=404 + 1000 * rank, n_trees=n_trees)
+    small = args.workload == "batched_small"
+    if small:
+        probs = synth.batched_small(seed_base=606 + 1000 * rank)
+        n_trees = len(probs)
+    else:
+        n_trees = int(os.environ.get("MIG_BATCH_TREES", "64"))
+        probs = synth.batched(seed_base=404 + 1000 * rank, n_trees=n_trees)
     stream = torch.cuda.Stream(local)
     ctx = mig.Context(local, stream=stream)
-    maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in probs]
+    dev_maps = {}  # one device map per distinct map (small trees share their map)
+    for p in probs:
+        if id(p.map) not in dev_maps:
+            dev_maps[id(p.map)] = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
+    maps = [dev_maps[id(p.map)] for p in probs]
     trees = [(p.tree.parent, p.tree.pos, p.sensor) for p in probs]
     rays = sum(p.tree.n * p.sensor.yaw_bins * p.sensor.width * p.sensor.height for p in probs)
     nodes = sum(p.tree.n for p in probs)
@@ -426,13 +435,17 @@ def run_batched(args):
                "warmup": args.warmup, "ms_per_step": tbatch / len(tb) * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 fixed point (u8 map)",
                "data": "synthetic (seeded; stands in for the paper's Gazebo worlds)",
-               "config": {"workload": f"batched: {n_trees} trees on {n_trees} rooms maps 400x400x100 @0.1 m, "
-                                      "trees U[50,2000] nodes, depth U[3,15], ray grids 64x48..320x240, K=16, 6 m",
-                          "nodes": nodes, "rays_per_step": rays, "l2": "inputs (64 maps, 1 GB) larger than L2",
+               "config": {"workload": (f"batched small trees: {n_trees} trees, 16 per map on {len(dev_maps)} rooms maps "
+                                       "400x400x100 @0.1 m, trees U[20,60] nodes, depth U[2,5], 64x48 rays, K=16, 6 m "
+                                       "(short-horizon replans; not one of the paper's configurations)") if small else
+                                      (f"batched: {n_trees} trees on {n_trees} rooms maps 400x400x100 @0.1 m, "
+                                       "trees U[50,2000] nodes, depth U[3,15], ray grids 64x48..320x240, K=16, 6 m"),
+                          "nodes": nodes, "rays_per_step": rays,
+                          "l2": f"inputs ({len(dev_maps)} maps, {len(dev_maps) * 16} MB) larger than L2",
                           "parallelism": f"replicas x{ws}"},
                "replans_per_s": ws * n_trees * len(tb) / tbatch,
                "plain": {"ms_per_step": tplain * 1e3, "rays_per_s": rays / tplain,
-                         "replans_per_s": n_trees / tplain, "launches": "64 sequential mig_tree_eval calls"},
+                         "replans_per_s": n_trees / tplain, "launches": f"{n_trees} sequential mig_tree_eval calls"},
                "batched_vs_plain_speedup": tplain / (tbatch / len(tb)),
                "results_identical_to_plain": bool(same),
                "graph": {"captures": caps, "replays": reps},
@@ -441,9 +454,10 @@ def run_batched(args):
                "e2e": {"value": value, "unit": "rays/s",
                        "h2d_bytes_per_step": int(sum(p.tree.n * 16 for p in probs)),
                        "d2h_bytes_per_step": int(nodes * 12)},
-               "gpu_launches": 1,
+               "gpu_launches": int(len(tb) * (sum(3 * (int(p.tree.depth().max()) + 1) - 1 for p in probs)
+                                             if best_engine == 1 else 1)),
                "clocks": clocks}
-    for m in maps:
+    for m in dev_maps.values():
         m.close()
     ctx.close()
     if ws > 1:
@@ -641,7 +655,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_scale",
-                    choices=["paper_scale", "tiny", "large", "batched", "serving"])
+                    choices=["paper_scale", "tiny", "large", "batched", "batched_small", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison (interval, absolute)")
     args = ap.parse_args()
@@ -651,7 +665,7 @@ def main():
         if res is not None:
             print(json.dumps(res))
         return
-    if args.workload == "batched":
+    if args.workload in ("batched", "batched_small"):
         res = run_batched(args)
     elif args.workload == "serving":
         res = run_serving(args)

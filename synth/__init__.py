@@ -473,6 +473,39 @@ def batched(seed_base=404, n_trees=64, n_range=(50, 2000), depth_range=(3, 15), 
         return list(ex.map(_batched_one, jobs))
 
 
+def _batched_small_one(args):
+    seed, trees_per_map, n_range, depth_range, grid = args
+    m, vps, rng = rooms_map(seed, scan_step_deg=1.0)
+    m.truth = None
+    out = []
+    for t in range(trees_per_map):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        dmax = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        n = min(n, sum(6 ** d for d in range(dmax + 1)) // 2)
+        start = vps[t % len(vps)]
+        tree = rrt(rng, m, start, n, dmax, 1.5, max_children=6, box=local_box(m, start, 8.0, 1.0, 1.5))
+        out.append(Problem(f"small_{seed}_{t}", m, tree, Sensor(90.0, 60.0, grid[0], grid[1], 6.0, 16, 0.0),
+                           {"seed": seed, "tree": t}))
+    return out
+
+
+def batched_small(seed_base=606, n_maps=16, trees_per_map=16, n_range=(20, 60), depth_range=(2, 5), grid=(64, 48),
+                  workers=None):
+    """Many short-horizon replans: n_maps seeded rooms maps (config-2 type), trees_per_map small trees on
+    each (U[20,60] nodes, depth limits U[2,5], 64x48 rays, K=16, 6 m), started from the map's scan
+    poses. Trees on the same map share its MapSpec object."""
+    jobs = [(seed_base + i, trees_per_map, n_range, depth_range, grid) for i in range(n_maps)]
+    workers = workers if workers is not None else min(16, os.cpu_count() or 1)
+    if workers <= 1 or n_maps <= 1:
+        groups = [_batched_small_one(j) for j in jobs]
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            groups = list(ex.map(_batched_small_one, jobs))
+    return [p for g in groups for p in g]
+
+
 def map_update_box(rng, m: MapSpec, frac=0.10):
     """One axis-aligned box holding `frac` of the grid's voxels, re-labelled from the
     ground truth (occupied stays occupied, the rest becomes free): a mapping update."""

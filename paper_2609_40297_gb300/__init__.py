@@ -396,9 +396,13 @@ def tree_eval_batch(ctx: Context, problems, maps, mode=MODE_MARGINAL):
 
 
 class Server:
-    """mig_server: continuous batching of replanning requests (worker thread in the library)."""
+    """mig_server: continuous batching of replanning requests (worker thread in the library).
 
-    def __init__(self, ctx: Context, arena_budget_bytes: int, max_inflight: int = 64):
+    max_inflight caps the requests evaluated together. Trees that each fill the GPU gain nothing
+    from wide interleaving and wait longer, so the default is small (4); raise it for many small
+    trees."""
+
+    def __init__(self, ctx: Context, arena_budget_bytes: int, max_inflight: int = 4):
         out = C.c_void_p()
         check(lib().mig_server_create(ctx.h, int(arena_budget_bytes), int(max_inflight), C.byref(out)))
         self.h = out

@@ -315,6 +315,13 @@ mig_status mig_tree_eval_stats(mig_map *map, int n, const int32_t *parent, const
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *mig_last_error(void);
 
+/* Build of this library (no counterpart in the paper). MIG_BUILD_CHECKED: built with
+ * MIG_DEBUG_BOUNDS=1, where every voxel load and depth-buffer write checks its index; an index
+ * outside its buffer skips the access and makes the host-array evaluation calls return MIG_ECUDA
+ * ("bounds check") instead of touching memory outside the buffer. Slower; for testing. */
+#define MIG_BUILD_CHECKED 1
+int mig_build_flags(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libmig.so")
 
 MIG_OK, MIG_EINVAL, MIG_ENOMEM, MIG_ECUDA, MIG_ETIMEOUT, MIG_EBUSY, MIG_ENOTFOUND = range(7)
 MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL, MODE_PANORAMIC = 0, 1, 2, 3, 4
+BUILD_CHECKED = 1  # mig_build_flags(): the bounds-checked build
 STATUS_NAMES = {0: "MIG_OK", 1: "MIG_EINVAL", 2: "MIG_ENOMEM", 3: "MIG_ECUDA", 4: "MIG_ETIMEOUT", 5: "MIG_EBUSY",
                 6: "MIG_ENOTFOUND"}
 
@@ -35,6 +36,7 @@ EXPORTS = [
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
     "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
+    "mig_build_flags",
 ]
 
 
@@ -152,6 +154,7 @@ def lib():
                 "mig_ctx_profile_read": (st, [p, p]),
                 "mig_tree_eval_stats": (st, [p, i, p, p, p, p, p, p, p]),
                 "mig_last_error": (C.c_char_p, []),
+                "mig_build_flags": (i, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name, None)

@@ -16,6 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmig.so")
+# checked build (MIG_DEBUG_BOUNDS=1: every voxel load and depth-buffer write checks its index)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libmig_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,20 +41,23 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, checked: bool = False) -> str:
+    """Compiles libmig.so (or, with checked=True, the bounds-checked libmig_checked.so)."""
+    out_dir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "mig.h")]
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               [os.path.join(ROOT, "include", "mig.h")])
     newest_dep = max(os.path.getmtime(p) for p in srcs + headers + [__file__])
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_dep:
-        return LIB
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest_dep:
+        return lib_path
     nv = nvcc()
-    base = flags()
+    base = flags(debug_bounds=checked)
     if ptxas_v:
         base = base + ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [nv, "-c", src, "-o", obj] + base
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -62,13 +68,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nv, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

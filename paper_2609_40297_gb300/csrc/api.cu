@@ -247,6 +247,14 @@ extern "C" {
 
 const char *mig_last_error(void) { return g_last_error.c_str(); }
 
+int mig_build_flags(void) {
+#if defined(MIG_DEBUG_BOUNDS) && MIG_DEBUG_BOUNDS
+    return MIG_BUILD_CHECKED;
+#else
+    return 0;
+#endif
+}
+
 mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocator, mig_ctx **out) {
     if (!out) return fail(MIG_EINVAL, "ctx_create: out is NULL");
     *out = nullptr;
@@ -554,7 +562,12 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = mode;
     p.max_anc = std::max(1, plan.max_depth);
+    p.arena_slots = std::max(1, plan.n_internal);
     if (pano) set_pano_params(p, cam, (int32_t *)(dev + o_pcnt));
+#if defined(MIG_DEBUG_BOUNDS) && MIG_DEBUG_BOUNDS
+    p.bounds_err = ctx->d_err + 16;  // checked build: out-of-buffer indices are recorded here
+    MIG_CUDA_TRY(cudaMemsetAsync(p.bounds_err, 0, 4, ctx->stream));
+#endif
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
         MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
@@ -585,6 +598,11 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     if (want_depth)
         MIG_CUDA_TRY(cudaMemcpyAsync(opts->depth_buffers, p.arena, (size_t)n * WH * 4, cudaMemcpyDeviceToHost, ctx->stream));
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+#if defined(MIG_DEBUG_BOUNDS) && MIG_DEBUG_BOUNDS
+    int32_t berr = 0;
+    MIG_CUDA_TRY(cudaMemcpy(&berr, p.bounds_err, 4, cudaMemcpyDeviceToHost));
+    if (berr) return fail(MIG_ECUDA, "bounds check: an index left its buffer (kinds " + std::to_string(berr) + ")");
+#endif
     std::memcpy(abs_gain, host, (size_t)n * 4);
     std::memcpy(marg_gain, host + (size_t)n * 4, (size_t)n * 4);
     std::memcpy(best_yaw, host + (size_t)n * 8, (size_t)n * 4);

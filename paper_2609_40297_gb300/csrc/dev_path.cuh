@@ -17,11 +17,6 @@
 #ifndef MIG_LAYOUT
 #define MIG_LAYOUT 1
 #endif
-// 1 = the batched ancestor test is an out-of-line call (its register needs do not add to the
-// DDA loop's), 0 = inlined.
-#ifndef MIG_OBS_NOINLINE
-#define MIG_OBS_NOINLINE 0
-#endif
 // 1 = the chunk's own-camera constants (projection rows, yaw cos/sin, node position) are read
 // from the warp's shared-memory slot at each use instead of being held in registers.
 #ifndef MIG_CAM_SMEM
@@ -32,18 +27,55 @@
 #ifndef MIG_COUNT_BLOCK
 #define MIG_COUNT_BLOCK 4
 #endif
-#ifndef MIG_COUNT_UNROLL
-#define MIG_COUNT_UNROLL 1
-#endif
 // Minimum resident count-kernel CTAs per SM requested from the register allocator.
 #ifndef MIG_COUNT_MINB
 #define MIG_COUNT_MINB 4
+#endif
+
+#ifndef MIG_DEBUG_BOUNDS
+#define MIG_DEBUG_BOUNDS 0
 #endif
 
 namespace mig {
 namespace dev {
 
 constexpr int kOcc = 2;
+
+// Checked builds (MIG_DEBUG_BOUNDS=1): an index outside its buffer sets `bit` in *err (when err is
+// not NULL) and the access is skipped; other builds compile the check away.
+constexpr int kBoundsVoxel = 1, kBoundsArena = 2, kBoundsDepth = 4;
+__device__ __forceinline__ bool in_bounds(int32_t *err, bool ok, int bit) {
+#if MIG_DEBUG_BOUNDS
+    if (!ok && err) atomicOr(err, bit);
+    return ok;
+#else
+    (void)err;
+    (void)ok;
+    (void)bit;
+    return true;
+#endif
+}
+
+__device__ __forceinline__ uint32_t grid_cells(int nx, int ny, int nz) {
+#if MIG_LAYOUT == 1
+    return (uint32_t)nx * (uint32_t)ny * (uint32_t)nz;
+#else
+    return (uint32_t)((nx + 7) >> 3) * (uint32_t)((ny + 7) >> 3) * (uint32_t)((nz + 7) >> 3) * 512u;
+#endif
+}
+
+// The code of the ray's current voxel (an occupied code for a checked build's skipped access).
+__device__ __forceinline__ uint8_t load_code(const uint8_t *g, uint32_t a, const GridView &G, int32_t *err) {
+    if (!in_bounds(err, a < grid_cells(G.nx, G.ny, G.nz), kBoundsVoxel)) return (uint8_t)kOcc;
+    return __ldg(g + a);
+}
+
+// Depth-buffer arena write of one pixel of the buffer in slot `slot`.
+__device__ __forceinline__ void arena_store(uint32_t *arena, int slots, int slot, size_t texel, size_t WH, uint32_t v,
+                                            int32_t *err) {
+    if (!in_bounds(err, slot >= 0 && (slots == 0 || slot < slots) && texel < WH, kBoundsArena)) return;
+    arena[(size_t)slot * WH + texel] = v;
+}
 constexpr int kUnknown = 0;
 constexpr uint32_t kQ16 = 65536;
 
@@ -228,13 +260,9 @@ __device__ __forceinline__ int floor_div_from(int64_t U, int64_t Z, float est, i
 }
 
 // Sec. IV-B: is the centre of voxel (x, y, z) observed by any ancestor (z <= stored depth)?
-#if MIG_OBS_NOINLINE
-#define MIG_OBS_INLINE __noinline__
-#else
-#define MIG_OBS_INLINE __forceinline__
-#endif
+// (The depth texel index is inside the buffer by construction: both pixel coordinates are clamped.)
 template <bool STATS, class HOT>
-__device__ MIG_OBS_INLINE bool observed(const HOT &p, const AncRec *anc, int na, int x, int y, int z,
+__device__ __forceinline__ bool observed(const HOT &p, const AncRec *anc, int na, int x, int y, int z,
                                          uint32_t &st_anc, uint32_t &st_reads) {
     const float xf = small_int_to_float(x), yf = small_int_to_float(y), zf = small_int_to_float(z);
     for (int a = 0; a < na; ++a) {
@@ -433,14 +461,10 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
             }
         }
         int cnt = 0;
-#if MIG_COUNT_UNROLL
 #pragma unroll
-#else
-#pragma unroll 1
-#endif
         for (int sidx = 0; sidx < kCountBlock; ++sidx) {
             if (have) {
-                const uint8_t code = __ldg(hp.g() + ray_addr(r, p.grid));
+                const uint8_t code = load_code(hp.g(), ray_addr(r, p.grid), p.grid, p.bounds_err);
                 if constexpr (STATS) ++st_steps;
                 if (code == kOcc) {
                     have = false;
@@ -545,7 +569,7 @@ __device__ __forceinline__ void count_chunk(const LevelParams &p, const HOT &hp,
         bool owned = false;
         unsigned long long samp = 0;
         if (have) {
-            const uint8_t code = __ldg(hp.g() + ray_addr(r, p.grid));
+            const uint8_t code = load_code(hp.g(), ray_addr(r, p.grid), p.grid, p.bounds_err);
             if constexpr (STATS) ++st_steps;
             if (code == kOcc) {
                 have = false;
@@ -664,7 +688,7 @@ __device__ __forceinline__ uint32_t render_pixel(const LevelParams &p, int n, co
     uint32_t ne = 0, ade = 1, steps = 0;
     bool hit = false;
     for (;;) {
-        const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+        const uint8_t code = load_code(p.grid.g, ray_addr(r, p.grid), p.grid, p.bounds_err);
         ++steps;
         if (code == kOcc) {
             hit = true;
@@ -672,7 +696,8 @@ __device__ __forceinline__ uint32_t render_pixel(const LevelParams &p, int n, co
         }
         if (!ray_step<true>(r, ne, ade)) break;
     }
-    p.arena[(size_t)nd.w * p.W * p.H + (size_t)tj * p.W + ti] = hit_depth(hit, ne, ade, b.w, p.Tq);
+    arena_store(p.arena, p.arena_slots, nd.w, (size_t)tj * p.W + ti, (size_t)p.W * p.H, hit_depth(hit, ne, ade, b.w, p.Tq),
+                p.bounds_err);
     return steps;
 }
 
@@ -715,10 +740,11 @@ __device__ __forceinline__ void render_chunk(const LevelParams &p, int n, int ti
             continue;
         }
         if (have) {
-            const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+            const uint8_t code = load_code(p.grid.g, ray_addr(r, p.grid), p.grid, p.bounds_err);
             const bool hit = code == kOcc;
             if (hit || !ray_step<true>(r, ne, ade)) {
-                p.arena[(size_t)nd.w * p.W * p.H + (size_t)tj * p.W + ti] = hit_depth(hit, ne, ade, dzc, p.Tq);
+                arena_store(p.arena, p.arena_slots, nd.w, (size_t)tj * p.W + ti, (size_t)p.W * p.H,
+                            hit_depth(hit, ne, ade, dzc, p.Tq), p.bounds_err);
                 have = false;
             }
         }

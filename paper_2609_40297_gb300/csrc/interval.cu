@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
             bool owned = false;
             unsigned long long key = 0;
             if (have) {
-                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+                const uint8_t code = load_code(p.grid.g, ray_addr(r, p.grid), p.grid, p.bounds_err);
                 if constexpr (STATS) ++st_steps;
                 if (code == kOcc) {
                     have = false;

@@ -43,6 +43,10 @@ struct LevelParams {
     const int4 *pano_dir;       // A*H: ray of cell (column, row) (Q30), pad
     const int4 *pano_row;       // A*2: strip rows (mv0 mv1 mv2 mz0) (mz1 mz2 - -) (Q16)
     int32_t *pano_cnt;          // n*A*2 (abs, excl) per column
+    // checked builds (MIG_DEBUG_BOUNDS=1): out-of-buffer indices are or-ed into *bounds_err (NULL:
+    // not recorded) and the access is skipped; arena_slots = depth buffers in the arena (0: unchecked)
+    int32_t *bounds_err;
+    int arena_slots;
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);

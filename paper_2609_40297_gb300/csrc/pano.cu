@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) pano_count_kernel(const LevelP
             bool owned = false;
             unsigned long long samp = 0;
             if (have) {
-                const uint8_t code = __ldg(p.grid.g + ray_addr(r, p.grid));
+                const uint8_t code = load_code(p.grid.g, ray_addr(r, p.grid), p.grid, p.bounds_err);
                 if constexpr (STATS) ++st_steps;
                 if (code == kOcc) {
                     have = false;

@@ -7,7 +7,9 @@
  *
  *   - the depth-buffer method (Sec. IV-A..C), restated step by step over the tree in
  *     depth order, with the integer readings listed in the design notes (all decisions are
- *     integer: quantised inputs, exact rational DDA, exact integer projection);
+ *     integer: quantised inputs, exact rational DDA, exact integer projection), in its modes:
+ *     marginal with voxel-centre samples, single parent, absolute, the paper's screen-space
+ *     interval overlap (Eq. 5-7, the literal per-ancestor pixel walk) and panoramic counting;
  *   - the visible-voxel sets I(n, psi) of Eq. 1, and the exact marginal gain of Eq. 2 by a
  *     depth-first walk with per-voxel reference counts (route 2 of the exact reference; the
  *     hash-set merge of Sec. I / Sec. IV-E is route 1, in oracle/exact.py).

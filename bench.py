@@ -625,6 +625,20 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=Fal
                 repi["nodes"] = m
                 repi["same_yaw_as_samples"] = float(np.mean(iv["yaw"][sel] == db["yaw"][sel]))
                 out[key] = repi
+            # the exact-yaw variant (each node's yaw chosen by its exact Eq. 2 gain, given its
+            # ancestors' exact choices), on the nodes of depth <= 4: how often the depth-buffer
+            # method picks the same viewpoint, and the exact gain of both choices of yaws
+            m4 = (d <= min(4, sample_depth)).astype(np.uint8)
+            s4 = m4.astype(bool)
+            ey, eE = oracle.exact_yaw(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent,
+                                      prob.tree.pos, s, node_mask=m4)
+            off, ids = oracle.visible_sets(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.pos,
+                                           db["yaw"], s, node_mask=m4)
+            edb = oracle.exact_dfs(prob.tree.parent, off, ids, prob.map.grid.size, node_mask=m4)
+            out["exact_yaw"] = {"nodes": int(s4.sum()), "same_yaw_as_depth_buffer": float(np.mean(ey[s4] == db["yaw"][s4])),
+                                "exact_gain_with_depth_buffer_yaws": int(edb[s4].sum()),
+                                "exact_gain_with_exact_yaws": int(eE[s4].sum()),
+                                "ratio": float(edb[s4].sum() / max(1, eE[s4].sum()))}
     return out
 
 
@@ -681,7 +695,7 @@ def main():
             cb = cpu_baseline(args.workload, with_gap=True, with_mode_gaps=not args.no_modes)
             res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
             res["gap_to_exact"] = cb.get("gap_to_exact")
-            for key in ("gap_to_exact_intervals", "gap_to_exact_panoramic"):
+            for key in ("gap_to_exact_intervals", "gap_to_exact_panoramic", "exact_yaw"):
                 if cb.get(key):
                     res[key] = cb[key]
         print(json.dumps(res))

@@ -84,6 +84,7 @@ def lib():
             L.oracle_pano_tables.argtypes = [f, f, i, i, i, f, p, p, p, p, p]
             L.oracle_pano_cells.argtypes = [f, f, i, i, i, f, p, i, p, p]
             L.oracle_pano_node_columns.argtypes = [p, i, i, i, p, f, f, i, i, i, f, C.c_int64, p]
+            L.oracle_exact_yaw.argtypes = [p, i, i, i, f, p, i, p, p, f, f, i, i, f, i, f, p, p, p, i]
             _lib = L
     return _lib
 
@@ -318,6 +319,26 @@ def visible_sets(grid, voxel, origin, pos, yaws, sensor, node_mask=None, n_threa
     if rc != 0:
         raise OracleError("oracle_visible_sets failed")
     return offsets, ids[:int(offsets[-1])]
+
+
+def exact_yaw(grid, voxel, origin, parent, pos, sensor, node_mask=None, n_threads=0):
+    """The exact-yaw variant: each node takes the yaw maximising its exact marginal gain (Eq. 2)
+    given its ancestors' own exact choices. Returns (yaw, E) int32 [n] (-1 outside node_mask)."""
+    grid = _c(grid, np.uint8)
+    nz, ny, nx = grid.shape
+    parent = _c(parent, np.int32)
+    pos = _c(pos, np.float32).reshape(-1, 3)
+    n = parent.shape[0]
+    yaw = np.full(n, -1, np.int32)
+    E = np.full(n, -1, np.int32)
+    mask = None if node_mask is None else _c(node_mask, np.uint8)
+    rc = lib().oracle_exact_yaw(_ptr(grid), nx, ny, nz, float(voxel), _ptr(_c(origin, np.float32)), n, _ptr(parent),
+                                _ptr(pos), float(sensor.hfov_deg), float(sensor.vfov_deg), sensor.width, sensor.height,
+                                float(sensor.range_m), sensor.yaw_bins, float(sensor.pitch_deg), _ptr(mask), _ptr(yaw),
+                                _ptr(E), int(n_threads))
+    if rc != 0:
+        raise OracleError(f"oracle_exact_yaw failed: {rc}")
+    return yaw, E
 
 
 def exact_dfs(parent, offsets, ids, nvox, node_mask=None):

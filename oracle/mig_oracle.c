@@ -1117,6 +1117,114 @@ int oracle_visible_sets(const uint8_t *grid, int nx, int ny, int nz, float voxel
     return bad ? -1 : 0;
 }
 
+/* The exact-yaw variant (Eq. 2 with the yaw chosen by the exact gain itself, Sec. III-B's
+ * argmax over the yaw set): depth-first over the tree with a dense per-voxel reference count of
+ * the sets on the current root path (as route 2); entering node n, every yaw's visible set
+ * I(n, k) is built (the same owner-visible sets as Eq. 1), E_k = the number of its voxels whose
+ * count is zero, psi = the lowest k maximising E_k, and I(n, psi) joins the path. Outputs psi and
+ * E(n) = E_psi per node (nodes outside node_mask: -1). */
+int oracle_exact_yaw(const uint8_t *grid, int nx, int ny, int nz, float voxel, const float *origin,
+                     int n, const int32_t *parent, const float *pos,
+                     float hfov, float vfov, int W, int H, float range_m, int K, float pitch,
+                     const uint8_t *node_mask, int32_t *yaw_out, int32_t *E_out, int n_threads) {
+    if (n == 0) return 0;
+    cam_t cam;
+    int rc = cam_build(&cam, hfov, vfov, W, H, K, pitch);
+    if (rc) return rc;
+    i64 Tq = llrint(((double)range_m / (double)voxel) * 65536.0);
+    grid_t G = {grid, {nx, ny, nz}};
+    int dims[3] = {nx, ny, nz};
+    size_t nvox = (size_t)nx * ny * nz;
+    i64 (*P)[3] = malloc((size_t)n * sizeof(*P));
+    uint16_t *cnt = calloc(nvox, sizeof(uint16_t));
+    int *head = malloc((size_t)n * sizeof(int)), *next = malloc((size_t)n * sizeof(int));
+    int *stack = malloc((size_t)n * 2 * sizeof(int));
+    int32_t **chosen = calloc((size_t)n, sizeof(int32_t *));
+    i64 *chosen_n = calloc((size_t)n, sizeof(i64));
+    int32_t **sets = calloc((size_t)K, sizeof(int32_t *));
+    i64 *set_n = calloc((size_t)K, sizeof(i64)), *set_cap = calloc((size_t)K, sizeof(i64));
+    if (!P || !cnt || !head || !next || !stack || !chosen || !chosen_n || !sets || !set_n || !set_cap) { rc = -2; goto done; }
+    for (int i = 0; i < n; ++i)
+        if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P[i])) { rc = -1; goto done; }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    int root = -1;
+    for (int i = 0; i < n; ++i) { head[i] = -1; yaw_out[i] = -1; E_out[i] = -1; }
+    for (int i = n - 1; i >= 0; --i) {
+        if (parent[i] < 0) root = i;
+        else { next[i] = head[parent[i]]; head[parent[i]] = i; }
+    }
+    if (root < 0) { rc = -1; goto done; }
+    int sp = 0;
+    stack[sp++] = root; /* entries: node (enter) or ~node (leave) */
+    while (sp > 0 && rc == 0) {
+        int e = stack[--sp];
+        if (e >= 0) {
+            int nd = e;
+            if (node_mask && !node_mask[nd]) continue;
+            /* every yaw's visible set, in parallel over the yaws */
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int k = 0; k < K; ++k) {
+                set_ctx sc = {&cam, k, 0, 0, P[nd], nx, ny, NULL, 0, 0};
+                for (int pass = 0; pass < 2; ++pass) { /* count, then fill */
+                    sc.count = 0;
+                    if (pass == 1) {
+                        if (set_cap[k] < sc.cap) {
+                            free(sets[k]);
+                            sets[k] = malloc((size_t)(sc.cap > 0 ? sc.cap : 1) * 4);
+                            set_cap[k] = sets[k] ? sc.cap : 0;
+                        }
+                        sc.ids = sets[k];
+                    }
+                    for (int j = 0; j < H; ++j)
+                        for (int i = 0; i < W; ++i) {
+                            size_t p = (size_t)j * W + i;
+                            i64 dvec[3];
+                            cam_dir(&cam, k, p, dvec);
+                            sc.pi = i; sc.pj = j;
+                            dda(&G, P[nd], dvec, Tq, cam.dzc[p], set_visit, &sc, NULL);
+                        }
+                    if (pass == 0) sc.cap = sc.count;
+                }
+                set_n[k] = sc.count;
+            }
+            int kb = 0;
+            i64 eb = -1;
+            for (int k = 0; k < K; ++k) {
+                if (!sets[k] && set_n[k] > 0) { rc = -2; break; }
+                i64 z = 0;
+                for (i64 q = 0; q < set_n[k]; ++q) if (cnt[sets[k][q]] == 0) z++;
+                if (MUT(20) ? z >= eb : z > eb) { eb = z; kb = k; }
+            }
+            if (rc) break;
+            yaw_out[nd] = kb;
+            E_out[nd] = (int32_t)eb;
+            chosen[nd] = malloc((size_t)(set_n[kb] > 0 ? set_n[kb] : 1) * 4);
+            if (!chosen[nd]) { rc = -2; break; }
+            memcpy(chosen[nd], sets[kb], (size_t)set_n[kb] * 4);
+            chosen_n[nd] = set_n[kb];
+            for (i64 q = 0; q < chosen_n[nd]; ++q) cnt[chosen[nd][q]]++;
+            stack[sp++] = ~nd;
+            for (int c = head[nd]; c >= 0; c = next[c]) stack[sp++] = c;
+        } else {
+            int nd = ~e;
+            for (i64 q = 0; q < chosen_n[nd]; ++q) cnt[chosen[nd][q]]--;
+            free(chosen[nd]);
+            chosen[nd] = NULL;
+        }
+    }
+done:
+    if (chosen) for (int i = 0; i < n; ++i) free(chosen[i]);
+    if (sets) for (int k = 0; k < K; ++k) free(sets[k]);
+    free(chosen); free(chosen_n); free(sets); free(set_n); free(set_cap);
+    free(P); free(cnt); free(head); free(next); free(stack);
+    cam_free(&cam);
+    return rc;
+}
+
 /* Route 2 of the exact marginal gain (Eq. 2): depth-first over the tree with a dense
  * per-voxel reference count of the sets on the current root path. E(n) = number of
  * voxels of I(n) whose count is zero when n is entered. */

@@ -8,16 +8,17 @@ that double counts, and in the interval mode (Eq. 5-7): a depth sample at the po
 entry instead of its midpoint, a screen parameter without perspective correction, a strict
 depth comparison, and a voxel sample at the voxel's entry instead of its traversal midpoint;
 in the panoramic mode: a wedge test that includes its upper boundary (double ownership) and
-a yaw window shifted by one column."""
+a yaw window shifted by one column; in the exact-yaw variant, the highest yaw on ties."""
 import pytest
 
 import oracle
+import test_oracle_exact_yaw as xpins  # noqa: E402
 import test_oracle_interval as ipins  # noqa: E402
 import test_oracle_pano as ppins  # noqa: E402
 import test_oracle_pins as pins  # noqa: E402
 from synth import Sensor
 
-MUTANTS = list(range(1, 20))
+MUTANTS = list(range(1, 21))
 
 PIN_CALLS = [
     lambda o: pins.test_dda_matches_exact_slab_brute_force(o),
@@ -49,6 +50,8 @@ PIN_CALLS = [
     lambda o: ppins.test_pano_owner_set_equals_voxel_centric_brute_force(o, 3),
     lambda o: ppins.test_pano_window_sums_and_identity(o, ppins.SENSORS[2]),
     lambda o: ppins.test_pano_mode_invariants(o, 1),
+    lambda o: xpins.test_exact_yaw_matches_hash_set_walk(o, 3),
+    lambda o: xpins.test_exact_yaw_special_cases(o),
 ]
 
 

@@ -303,6 +303,14 @@ typedef struct mig_kernel_times {
 mig_status mig_ctx_profile(mig_ctx *ctx, int enable);
 mig_status mig_ctx_profile_read(mig_ctx *ctx, mig_kernel_times *out);
 
+/* Random-gather probe: the rate (loads per second) at which the device serves independent loads
+ * of elem_bytes (1 or 4) from pseudo-random positions of a buffer of buffer_bytes (rounded down to
+ * a power-of-two element count; 4 KiB .. 4 GiB), L1 bypassed, so that each load is one sector
+ * request: L2-served when the buffer fits in L2, HBM-served otherwise. The ceiling for the count
+ * pass's scattered voxel (1 B) and depth-texel (4 B) gathers. Allocates and frees its buffer on the
+ * context; synchronous. Errors: MIG_EINVAL, MIG_ENOMEM, MIG_ECUDA. */
+mig_status mig_probe_gather(mig_ctx *ctx, uint64_t buffer_bytes, int elem_bytes, double *loads_per_s);
+
 typedef struct mig_eval_stats {
     uint64_t rays, dda_steps, unknown_visits, samples, ancestor_tests, depth_reads;
     uint64_t render_rays, render_steps;

@@ -36,7 +36,7 @@ EXPORTS = [
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
     "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
-    "mig_build_flags",
+    "mig_build_flags", "mig_probe_gather",
 ]
 
 
@@ -155,6 +155,7 @@ def lib():
                 "mig_tree_eval_stats": (st, [p, i, p, p, p, p, p, p, p]),
                 "mig_last_error": (C.c_char_p, []),
                 "mig_build_flags": (i, []),
+                "mig_probe_gather": (st, [p, C.c_uint64, i, p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name, None)
@@ -332,6 +333,13 @@ def tree_eval(m: Map, parent, pos, sensor, mode=MODE_MARGINAL, want_counts=False
     check(lib().mig_tree_eval_ex(m.h, n, _ptr(parent), _ptr(pos), C.byref(s), C.byref(opts), _ptr(out["abs"]),
                                  _ptr(out["marg"]), _ptr(out["yaw"])))
     return out
+
+
+def probe_gather(ctx: Context, buffer_bytes: int, elem_bytes: int = 1) -> float:
+    """mig_probe_gather: random independent loads per second from a buffer of buffer_bytes."""
+    out = C.c_double()
+    check(lib().mig_probe_gather(ctx.h, int(buffer_bytes), int(elem_bytes), C.byref(out)))
+    return out.value
 
 
 def tree_eval_stats(m: Map, parent, pos, sensor):

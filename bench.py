@@ -341,7 +341,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Gop/s",
                          "frac": achieved_ops / peak_ops, "traffic": traffic, "kernel": "count_kernel",
                          "algorithmic_ops_per_launch": alg_ops_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                         "peak_source": "issue ceiling 152 SMs x 128 lanes x SM clock under load (design notes)",
+                         "peak_source": "issue ceiling: 152 SMs x 4 schedulers x 32 lanes x the SM clock sampled under load",
                          "note": f"ops/unit: DDA step {OPS_PER_STEP}, owner test {OPS_PER_OWNER_TEST}, "
                                  f"ancestor projection {OPS_PER_ANCESTOR_TEST}; traffic = ncu DRAM bytes of one "
                                  "launch (level 8) when the committed summary matches the kernel source"},

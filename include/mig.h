@@ -20,8 +20,10 @@
  *  - World frame z-up; yaw bin k is psi_k = 2 pi k / K counter-clockwise from +x; camera
  *    x right, y down, z forward; pitch positive = nose down; pinhole with principal point at
  *    the image centre and rays through pixel centres (Eq. 5).
- *  - The exact integer arithmetic is specified in the project's design notes; results are
- *    deterministic and identical on every run.
+ *  - Every result-deciding step is exact integer arithmetic (positions quantised to Q16 voxel
+ *    units, ray directions Q30, projection rows Q16, the DDA's crossings compared as exact
+ *    rationals), except the interval mode's fixed sequence of correctly rounded single-precision
+ *    operations: results are deterministic and identical on every run.
  */
 #ifndef MIG_H
 #define MIG_H

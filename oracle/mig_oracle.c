@@ -6,7 +6,7 @@
  * includes none of its headers; it is a plain, slow, direct statement of the method:
  *
  *   - the depth-buffer method (Sec. IV-A..C), restated step by step over the tree in
- *     depth order, with the integer readings listed in the design notes (all decisions are
+ *     depth order, with integer readings of the paper's unstated details (all decisions are
  *     integer: quantised inputs, exact rational DDA, exact integer projection), in its modes:
  *     marginal with voxel-centre samples, single parent, absolute, the paper's screen-space
  *     interval overlap (Eq. 5-7, the literal per-ancestor pixel walk) and panoramic counting;

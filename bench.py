@@ -108,10 +108,14 @@ def l2_flush_buffer(torch, dev):
 
 
 def kernel_source_hash():
+    """Hash of the count kernel's code (its source files with comments and blank lines removed), so
+    that an ncu summary stays tied to the code it measured, not to its comments."""
     h = hashlib.sha256()
     for f in ("kernels.cu", "kernels.h", "dev_path.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f)) as fh:
+            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = [ln.split("//", 1)[0].rstrip() for ln in txt.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

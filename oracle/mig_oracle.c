@@ -475,7 +475,8 @@ static int interval_visit(void *vctx, const int32_t v[3], uint8_t code, const i6
  * two boundary vectors, Q30). Each column is a one-pixel-wide strip camera looking along the
  * wedge's centre azimuth, with the pinhole's rows (Eq. 5's v, focal length and principal point
  * from the vertical field of view); its rays pass through the strip's row centres. A voxel is
- * owned by the cell (column, row) containing its centre (the rule of reading A1), counted as
+ * owned by the cell (column, row) containing its centre (as a pinhole voxel is owned by the
+ * pixel containing its centre's projection), counted as
  * absolute gain for the column, and as marginal gain unless an ancestor's (pinhole) depth
  * buffer observes it. Yaw k sums the Wc = round(A hfov / 360) columns centred on its azimuth.
  * Level camera only (pitch 0): wedges are vertical half-planes.

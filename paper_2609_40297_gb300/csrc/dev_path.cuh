@@ -1,8 +1,9 @@
 // Device-side steps of the marginal-gain path, shared by the per-level kernels (kernels.cu)
 // and the batched persistent kernel (batch.cu): the integer DDA (Sec. IV-B), the owner test
-// (reading A1), the ancestor depth test (Sec. IV-B), yaw selection (Sec. III-B) and depth
-// rendering (Sec. IV-A). All result-deciding arithmetic is integer: positions Q16 voxel units,
-// ray directions Q30, projection rows Q16, depths Q16.16.
+// (a voxel counts only for the ray of the pixel containing its centre's projection), the
+// ancestor depth test (Sec. IV-B), yaw selection (Sec. III-B) and depth rendering (Sec. IV-A).
+// All result-deciding arithmetic is integer: positions Q16 voxel units, ray directions Q30,
+// projection rows Q16, depths Q16.16.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -228,7 +229,7 @@ __device__ __forceinline__ void decode_item(const LevelParams &p, int item, int 
 // Work item = (node of the level, yaw k, tile of tile_w x tile_h pixel rays), taken by one warp
 // from the level's atomic work counter (no CTA barrier: warps never wait for each other). Lane l
 // casts rays l, l+32, ... of the tile and starts its next ray as soon as the current one ends.
-// Unknown voxels owned by the ray (A1: the voxel centre projects into this pixel) count as
+// Unknown voxels owned by the ray (the voxel centre projects into this pixel) count as
 // absolute gain; their coordinates go to a per-warp queue, and each full batch of 32 samples is
 // tested against the ancestors' depth buffers with all 32 lanes at once (Sec. IV-B), so the
 // rare, long ancestor test never runs one lane at a time.

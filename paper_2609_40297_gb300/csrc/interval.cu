@@ -1,9 +1,10 @@
 // Interval-mode count pass: the paper's screen-space overlap test (Sec. IV-B, Eq. 5-7).
 //
 // For every candidate ray the 3D DDA (Sec. IV-B) visits voxels exactly as in the sample mode;
-// each owned unknown voxel (reading A1) counts as absolute gain and becomes a sample at the
-// midpoint of the ray's traversal of it. A sample is excluded from the marginal gain when it
-// lies in the union of the ancestors' overlap intervals of the ray. For each ancestor the ray is
+// each owned unknown voxel (its centre projects into the ray's pixel) counts as absolute gain and
+// becomes a sample at the midpoint of the ray's traversal of it. A sample is excluded from the
+// marginal gain when it lies in the union of the ancestors' overlap intervals of the ray. For
+// each ancestor the ray is
 //   1. taken to the ancestor's camera as projective image coordinates (U, V, Z), exact integers
 //      from the Q16 projection rows, then IEEE single precision in voxel units;
 //   2. clipped to the valid depth range [Z_NEAR, range];
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
                 } else {
                     if (code == kUnknown) {
                         if constexpr (STATS) ++st_unk;
-                        // owner test (reading A1): the voxel centre projects into pixel (ti, tj)
+                        // owner test: the voxel centre projects into pixel (ti, tj)
                         const int rx = voxel_offset(r.nx, r.sx), ry = voxel_offset(r.ny, r.sy),
                                   rz = voxel_offset(r.nz, r.sz);
                         const int64_t Z = (int64_t)yk[8] * rx + (int64_t)yk[9] * ry + (int64_t)yk[10] * rz;

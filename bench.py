@@ -604,9 +604,10 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=False):
-    """The oracle as it stands, on this host's cores, on a bounded, ancestor-closed sample of
-    the workload (all nodes up to a depth), reported in the benchmark's unit."""
+def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=False, n_threads=0):
+    """The oracle as it stands, on this host's cores (n_threads = 0: all of them), on a bounded,
+    ancestor-closed sample of the workload (all nodes up to a depth), reported in the benchmark's
+    unit."""
     import oracle
     prob = make_problem(workload, 0)
     s = prob.sensor
@@ -617,10 +618,10 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=Fal
     m = int(mask.sum())
     t0 = time.perf_counter()
     db = oracle.eval_tree(prob.map.grid, prob.map.voxel_size, prob.map.origin, prob.tree.parent, prob.tree.pos, s,
-                          node_mask=mask)
+                          node_mask=mask, n_threads=n_threads)
     dt = time.perf_counter() - t0
     rays = m * s.yaw_bins * s.width * s.height
-    out = {"value": rays / dt, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+    out = {"value": rays / dt, "unit": "rays/s", "cores": n_threads or os.cpu_count(), "kind": "oracle",
            "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
                      f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
     if with_gap:
@@ -722,6 +723,10 @@ def main():
             for key in ("gap_to_exact_intervals", "gap_to_exact_panoramic", "exact_yaw"):
                 if cb.get(key):
                     res[key] = cb[key]
+            # the same oracle on one core, on a smaller sample (a few seconds)
+            c1 = cpu_baseline(args.workload, sample_depth={"tiny": 10, "paper_scale": 3, "large": 0}[args.workload],
+                              n_threads=1)
+            res["cpu_baseline_single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(res))
 
 

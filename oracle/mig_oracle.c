@@ -688,7 +688,7 @@ int oracle_eval_tree(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
     for (int i = 0; i < n; ++i) if (depth[i] > max_d) max_d = depth[i];
     size_t WH = (size_t)W * H;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());  /* 0 = every core */
 #else
     (void)n_threads;
 #endif
@@ -1089,7 +1089,7 @@ int oracle_visible_sets(const uint8_t *grid, int nx, int ny, int nz, float voxel
     for (int i = 0; i < n; ++i)
         if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P[i])) { free(P); cam_free(&cam); return -1; }
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());  /* 0 = every core */
 #else
     (void)n_threads;
 #endif
@@ -1148,7 +1148,7 @@ int oracle_exact_yaw(const uint8_t *grid, int nx, int ny, int nz, float voxel, c
     for (int i = 0; i < n; ++i)
         if (quantize_pos(pos + 3 * (size_t)i, origin, voxel, dims, P[i])) { rc = -1; goto done; }
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());  /* 0 = every core */
 #else
     (void)n_threads;
 #endif

@@ -352,6 +352,21 @@ def test_marginal_invariants(oracle_lib, seed):
     assert np.all((r["yaw"] >= 0) & (r["yaw"] < K))
 
 
+def test_result_independent_of_thread_count(oracle_lib):
+    """The oracle parallelises over the nodes of a level and the yaws of a node; each (node, yaw)
+    count is written by one thread, so one core and every core give the same result in every mode,
+    and a one-thread call leaves later calls on every core."""
+    p = synth.tiny()
+    for mode in (oracle_lib.MODE_MARGINAL, oracle_lib.MODE_INTERVAL, oracle_lib.MODE_PANORAMIC):
+        one = oracle_lib.eval_tree(p.map.grid, p.map.voxel_size, p.map.origin, p.tree.parent, p.tree.pos, p.sensor,
+                                   mode=mode, want_counts=True, want_depth=True, n_threads=1)
+        every = oracle_lib.eval_tree(p.map.grid, p.map.voxel_size, p.map.origin, p.tree.parent, p.tree.pos, p.sensor,
+                                     mode=mode, want_counts=True, want_depth=True)
+        assert one.keys() == every.keys()
+        for k in one:
+            assert np.array_equal(one[k], every[k]), (mode, k)
+
+
 def test_fixed_yaw_ordering_abs_sp_all(oracle_lib):
     p = synth.random_small(4, n_nodes=14)
     s = Sensor(80, 55, 19, 13, 2.5, 1, 0.0)  # one yaw: every mode sees the same viewpoints

@@ -73,17 +73,15 @@ __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 
 // steps 1-3 for the candidate ray from P to its range endpoint E (Q16) and the ancestor at Pa
-// with projection rows m (Q16: mu, mv, mz); false if nothing of the ray is in view
+// with projection rows m (Q16: mu, mv, mz); false if nothing of the ray is in view, or if the
+// sample's ray fraction lam lies outside the depth-clipped range (seg_param would then reject it,
+// so the screen-space part is skipped with the same outcome)
 __device__ bool seg_setup(const int32_t *m, const int3 Pa, const int64_t P[3], const int64_t E[3], float zf, int W,
-                          int H, Seg &g) {
+                          int H, float lam, Seg &g) {
     const int64_t r0x = P[0] - Pa.x, r0y = P[1] - Pa.y, r0z = P[2] - Pa.z;
     const int64_t r1x = E[0] - Pa.x, r1y = E[1] - Pa.y, r1z = E[2] - Pa.z;
     const float sc = 2.3283064365386963e-10f;  // 2^-32: Q32 -> voxel units
-    const float U0 = fmul(__ll2float_rn((int64_t)m[0] * r0x + (int64_t)m[1] * r0y + (int64_t)m[2] * r0z), sc);
-    const float V0 = fmul(__ll2float_rn((int64_t)m[3] * r0x + (int64_t)m[4] * r0y + (int64_t)m[5] * r0z), sc);
     const float Z0 = fmul(__ll2float_rn((int64_t)m[6] * r0x + (int64_t)m[7] * r0y + (int64_t)m[8] * r0z), sc);
-    const float U1 = fmul(__ll2float_rn((int64_t)m[0] * r1x + (int64_t)m[1] * r1y + (int64_t)m[2] * r1z), sc);
-    const float V1 = fmul(__ll2float_rn((int64_t)m[3] * r1x + (int64_t)m[4] * r1y + (int64_t)m[5] * r1z), sc);
     const float Z1 = fmul(__ll2float_rn((int64_t)m[6] * r1x + (int64_t)m[7] * r1y + (int64_t)m[8] * r1z), sc);
     const float zn = kZNear;
     const float dZ = fsub(Z1, Z0);
@@ -107,6 +105,11 @@ __device__ bool seg_setup(const int32_t *m, const int3 Pa, const int64_t P[3], c
         if (h < hi) hi = h;
     }
     if (!(lo < hi)) return false;
+    if (!(lam >= lo && lam <= hi)) return false;
+    const float U0 = fmul(__ll2float_rn((int64_t)m[0] * r0x + (int64_t)m[1] * r0y + (int64_t)m[2] * r0z), sc);
+    const float V0 = fmul(__ll2float_rn((int64_t)m[3] * r0x + (int64_t)m[4] * r0y + (int64_t)m[5] * r0z), sc);
+    const float U1 = fmul(__ll2float_rn((int64_t)m[0] * r1x + (int64_t)m[1] * r1y + (int64_t)m[2] * r1z), sc);
+    const float V1 = fmul(__ll2float_rn((int64_t)m[3] * r1x + (int64_t)m[4] * r1y + (int64_t)m[5] * r1z), sc);
     const float dU = fsub(U1, U0), dV = fsub(V1, V0);
     const float Ua = fadd(U0, fmul(lo, dU)), Va = fadd(V0, fmul(lo, dV)), Za = fadd(Z0, fmul(lo, dZ));
     const float Ub = fadd(U0, fmul(hi, dU)), Vb = fadd(V0, fmul(hi, dV)), Zb = fadd(Z0, fmul(hi, dZ));
@@ -235,7 +238,7 @@ __device__ bool iv_observed(const LevelParams &p, const IvAnc *anc, int na, cons
         const IvAnc &A = anc[a];
         Seg g;
         if constexpr (STATS) ++st_seg;
-        if (!seg_setup(p.yawtab + A.yaw * 12 + 2, make_int3(A.px, A.py, A.pz), P, E, zf, p.W, p.H, g)) continue;
+        if (!seg_setup(p.yawtab + A.yaw * 12 + 2, make_int3(A.px, A.py, A.pz), P, E, zf, p.W, p.H, lam, g)) continue;
         float s;
         if (seg_param(g, lam, s) && seg_lookup(g, p.W, p.H, A.D, s)) return true;
     }

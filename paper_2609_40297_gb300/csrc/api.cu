@@ -485,6 +485,7 @@ mig_status mig_tree_check(int n, const int32_t *parent, int32_t *depth_out, int3
 static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const float *pos_m, const mig_sensor *sensor,
                             const mig_eval_opts *opts, mig_eval_stats *stats, int32_t *abs_gain, int32_t *marg_gain,
                             int32_t *best_yaw) {
+    NvtxRange range("mig_tree_eval");
     if (!m || !sensor) return fail(MIG_EINVAL, "tree_eval: map or sensor is NULL");
     if (n < 0) return fail(MIG_EINVAL, "tree_eval: negative node count");
     if (n > 0 && (!abs_gain || !marg_gain || !best_yaw)) return fail(MIG_EINVAL, "tree_eval: output array is NULL");
@@ -646,6 +647,7 @@ mig_status mig_tree_eval(mig_map *m, int n, const int32_t *parent, const float *
 
 mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const float *pos_m, const mig_sensor *sensor,
                                 int max_depth, int32_t *abs_gain, int32_t *marg_gain, int32_t *best_yaw) {
+    NvtxRange range("mig_tree_eval_device");
     if (!m || !sensor) return fail(MIG_EINVAL, "tree_eval_device: map or sensor is NULL");
     if (n < 0) return fail(MIG_EINVAL, "tree_eval_device: negative node count");
     if (max_depth < 0 || max_depth > MIG_MAX_DEPTH) return fail(MIG_EINVAL, "tree_eval_device: max_depth outside [0, 64]");

@@ -740,6 +740,7 @@ extern "C" void mig_batch_release(mig_ctx *ctx) {
 }
 
 extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_tree_desc *trees) {
+    NvtxRange range("mig_tree_eval_batch");
     if (!ctx || n_trees < 0 || (n_trees > 0 && !trees)) return fail(MIG_EINVAL, "tree_eval_batch: invalid argument");
     std::vector<BatchItem> items;
     items.reserve(n_trees);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstring>
@@ -150,8 +151,19 @@ void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int co
 // records an event pair around launch() on the context stream when profiling is on
 void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a);
 void prof_end(mig_ctx *ctx, int kind, cudaEvent_t a);
+// NVTX range on the host thread (visible to ncu --nvtx and to timeline profilers; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 template <class F>
 inline void timed_launch(mig_ctx *ctx, int kind, F &&launch) {
+    static const char *const kNames[kProfKinds] = {"mig count", "mig select", "mig render", "mig plan", "mig batch"};
+    NvtxRange range(kNames[kind]);
     cudaEvent_t a = nullptr;
     prof_begin(ctx, kind, &a);
     launch();

@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -604,6 +605,23 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it: the model name, or on Arm the implementer and part
+    codes (0x41 / 0xd4f is an Arm Neoverse V2, the Grace core), plus the machine type."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = (x.strip() for x in line.split(":", 1))
+                    fields.setdefault(k, v)
+    except OSError:
+        pass
+    name = fields.get("model name") or " ".join(
+        f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part") if k in fields)
+    return f"{platform.machine()}: {name or 'unknown'}"
+
+
 def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=False, n_threads=0):
     """The oracle as it stands, on this host's cores (n_threads = 0: all of them), on a bounded,
     ancestor-closed sample of the workload (all nodes up to a depth), reported in the benchmark's
@@ -621,7 +639,8 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=Fal
                           node_mask=mask, n_threads=n_threads)
     dt = time.perf_counter() - t0
     rays = m * s.yaw_bins * s.width * s.height
-    out = {"value": rays / dt, "unit": "rays/s", "cores": n_threads or os.cpu_count(), "kind": "oracle",
+    out = {"value": rays / dt, "unit": "rays/s", "cores": n_threads or os.cpu_count(), "cpu": cpu_model(),
+           "kind": "oracle",
            "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
                      f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
     if with_gap:
@@ -685,7 +704,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": cb["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64 fixed point (u8 map)", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload], "sample": cb["sample"]},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -718,7 +737,7 @@ def main():
     if rank == 0 and res is not None:
         if ws == 1 and not args.no_cpu_baseline and args.workload in ("paper_scale", "tiny", "large"):
             cb = cpu_baseline(args.workload, with_gap=True, with_mode_gaps=not args.no_modes)
-            res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")}
             res["gap_to_exact"] = cb.get("gap_to_exact")
             for key in ("gap_to_exact_intervals", "gap_to_exact_panoramic", "exact_yaw"):
                 if cb.get(key):
@@ -726,7 +745,7 @@ def main():
             # the same oracle on one core, on a smaller sample (a few seconds)
             c1 = cpu_baseline(args.workload, sample_depth={"tiny": 10, "paper_scale": 3, "large": 0}[args.workload],
                               n_threads=1)
-            res["cpu_baseline_single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            res["cpu_baseline_single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")}
         print(json.dumps(res))
 
 

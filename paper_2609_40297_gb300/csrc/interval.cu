@@ -24,9 +24,10 @@
 // before the sample's screen parameter (seg_lookup). The result is the walk's, bit for bit.
 //
 // Layout: one warp per work item (node, yaw, tile of rays), taken from the level's atomic work
-// counter; a lane takes the tile's next ray as soon as its ray ends. Owned samples (ray fraction,
-// pixel) go to a per-warp queue; each full batch of 32 is tested against the ancestors with one
-// sample per lane.
+// counter; a lane takes the tile's next ray as soon as its ray ends. Owned samples go to a
+// per-warp queue as the crossings that bound their voxel and their pixel; each full batch of 32 is
+// tested against the ancestors with one sample per lane, which is also where each sample's ray
+// fraction is computed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -224,14 +225,29 @@ __device__ bool seg_lookup(const Seg &g, int W, int H, const uint32_t *D, float 
     return fmul(wm, Dv) >= 1.0f;  // z <= D in inverse depth
 }
 
-// Is the sample (ray fraction lam of the ray through pixel pix, yaw ck / sk, origin P) inside an
-// ancestor's observed portions? Ancestors parent first; the ray's set-up is rebuilt per sample.
+// A queued sample: the face distances of the crossings that enter and leave its voxel (Q16), and
+// which of the ray's direction components |d_x|, |d_y|, |d_z| each is divided by (code 3: the
+// ray's start, entry at t = 0 written as 0 / 1), with the pixel. The ray fraction is computed from
+// it when the sample is tested, one sample per lane, not in the divergent DDA loop.
+__device__ __forceinline__ uint32_t speed_code(uint32_t ad, const RayIn &r) {
+    return ad == r.adx ? 0u : (ad == r.ady ? 1u : (ad == r.adz ? 2u : 3u));
+}
+__device__ __forceinline__ uint32_t speed_of(uint32_t code, uint32_t adx, uint32_t ady, uint32_t adz) {
+    return code == 0u ? adx : (code == 1u ? ady : (code == 2u ? adz : 1u));
+}
+
+// Is the queued sample e (ray through pixel e.z >> 4, yaw ck / sk, origin P) inside an ancestor's
+// observed portions? Ancestors parent first; the ray's set-up is rebuilt per sample.
 template <bool STATS>
 __device__ bool iv_observed(const LevelParams &p, const IvAnc *anc, int na, const int64_t P[3], int ck, int sk,
-                            float zf, float lam, int pix, uint32_t &st_seg) {
+                            float zf, float T, const uint4 e, uint32_t &st_seg) {
+    const int pix = (int)(e.z >> 4);
     const int4 b = p.body[pix];
     int dx, dy, dz;
     ray_dir(b, ck, sk, dx, dy, dz);
+    const uint32_t adx = (uint32_t)(dx < 0 ? -dx : dx), ady = (uint32_t)(dy < 0 ? -dy : dy),
+                   adz = (uint32_t)(dz < 0 ? -dz : dz);
+    const float lam = sample_lambda(e.x, speed_of(e.z & 3u, adx, ady, adz), e.y, speed_of((e.z >> 2) & 3u, adx, ady, adz), T);
     const int64_t E[3] = {P[0] + (((int64_t)p.Tq * dx) >> 30), P[1] + (((int64_t)p.Tq * dy) >> 30),
                           P[2] + (((int64_t)p.Tq * dz) >> 30)};
     for (int a = 0; a < na; ++a) {
@@ -248,11 +264,11 @@ __device__ bool iv_observed(const LevelParams &p, const IvAnc *anc, int na, cons
 template <bool STATS>
 __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel(const LevelParams p) {
     extern __shared__ IvAnc s_iv_anc[];
-    __shared__ unsigned long long s_q[kIvWarps][64];
+    __shared__ uint4 s_q[kIvWarps][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     IvAnc *anc = s_iv_anc + warp * p.max_anc;
-    unsigned long long *q = s_q[warp];
+    uint4 *q = s_q[warp];
     const int l0 = p.level_off[p.lvl];
     const int L = p.level_off[p.lvl + 1] - l0;
     const int items = L * p.K * p.tiles;
@@ -318,7 +334,7 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
                 continue;
             }
             bool owned = false;
-            unsigned long long key = 0;
+            uint4 key = make_uint4(0u, 0u, 0u, 0u);
             if (have) {
                 const uint8_t code = load_code(p.grid.g, ray_addr(r, p.grid), p.grid, p.bounds_err);
                 if constexpr (STATS) ++st_steps;
@@ -342,8 +358,8 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
                     uint32_t nx = 0, adx = 1;
                     const bool more = ray_step<true>(r, nx, adx);  // nx / adx: this voxel's exit crossing
                     if (owned)
-                        key = (unsigned long long)__float_as_uint(sample_lambda(ne, ade, nx, adx, T)) |
-                              ((unsigned long long)(uint32_t)(tj * p.W + ti) << 32);
+                        key = make_uint4(ne, nx, speed_code(ade, r) | (speed_code(adx, r) << 2) |
+                                                     ((uint32_t)(tj * p.W + ti) << 4), 0u);
                     ne = nx;
                     ade = adx;
                     have = more;
@@ -356,9 +372,7 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
                 qn += __popc(bal);
                 if (qn >= 32) {  // a full batch: every lane tests one sample against the ancestors
                     __syncwarp();
-                    const unsigned long long e = q[lane];
-                    c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, __uint_as_float((uint32_t)e),
-                                                 (int)(e >> 32), st_seg);
+                    c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, T, q[lane], st_seg);
                     __syncwarp();
                     if (lane < qn - 32) q[lane] = q[lane + 32];
                     __syncwarp();
@@ -368,9 +382,7 @@ __global__ void __launch_bounds__(kIvThreads, MIG_IV_MINB) interval_count_kernel
         }
         __syncwarp();
         if (lane < qn) {
-            const unsigned long long e = q[lane];
-            c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, __uint_as_float((uint32_t)e), (int)(e >> 32),
-                                         st_seg);
+            c_mrg += !iv_observed<STATS>(p, anc, na, P, ck, sk, zf, T, q[lane], st_seg);
         }
         c_abs = __reduce_add_sync(0xffffffffu, c_abs);
         c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);

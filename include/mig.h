@@ -301,7 +301,20 @@ void mig_server_destroy(mig_server *srv);
 typedef struct mig_kernel_times {
     double count_ms, select_ms, render_ms, plan_ms, batch_ms;
     uint64_t count_launches, select_launches, render_launches, plan_launches, batch_launches;
+    /* the owned-voxel count's two kernels (count_ms then covers the ray-by-ray, interval and
+     * panoramic count kernels only) */
+    double cast_ms, voxel_ms;
+    uint64_t cast_launches, voxel_launches;
 } mig_kernel_times;
+/* Count kernels of the sample modes (marginal, single parent, absolute; no counterpart in the
+ * paper, and both give identical results): ray_by_ray = 0 selects owned-voxel counting (the
+ * default: each pixel ray is cast to its stopping point once, then every unknown voxel of the
+ * frustum is tested against the ray of the pixel that owns it), 1 ray-by-ray counting (every ray
+ * owner-tests every unknown voxel it crosses). The owned-voxel kernels keep one uint16 step count
+ * per (node, yaw, pixel) of a level in a buffer of at most steps_budget_bytes (0 = the default,
+ * 1 GiB); a level whose pairs do not fit is counted in chunks (at least one pair per chunk).
+ * Errors: MIG_EINVAL (ctx NULL). */
+mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int ray_by_ray, uint64_t steps_budget_bytes);
 mig_status mig_ctx_profile(mig_ctx *ctx, int enable);
 mig_status mig_ctx_profile_read(mig_ctx *ctx, mig_kernel_times *out);
 
@@ -317,6 +330,12 @@ typedef struct mig_eval_stats {
     uint64_t rays, dda_steps, unknown_visits, samples, ancestor_tests, depth_reads;
     uint64_t render_rays, render_steps;
     uint64_t count_launches, render_launches;
+    /* the owned-voxel count's own work (zero when the context counts ray by ray): rays cast to
+     * their stopping point, voxel steps and brick jumps of those casts, voxels enumerated in the
+     * frusta, unknown ones among them, exact visit tests, counted samples (== samples), and the
+     * ancestor tests and depth reads of those samples */
+    uint64_t cast_rays, cast_steps, cast_jumps, voxel_candidates, voxel_unknown, visit_tests, owned_samples;
+    uint64_t voxel_ancestor_tests, voxel_depth_reads;
 } mig_eval_stats;
 mig_status mig_tree_eval_stats(mig_map *map, int n, const int32_t *parent, const float *pos_m,
                                const mig_sensor *sensor, mig_eval_stats *stats, int32_t *abs_gain,

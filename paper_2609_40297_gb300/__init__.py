@@ -36,7 +36,7 @@ EXPORTS = [
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
     "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
-    "mig_build_flags", "mig_probe_gather",
+    "mig_build_flags", "mig_probe_gather", "mig_ctx_set_count_kernel",
 ]
 
 
@@ -73,7 +73,8 @@ class KernelTimes(C.Structure):
     _fields_ = [("count_ms", C.c_double), ("select_ms", C.c_double), ("render_ms", C.c_double),
                 ("plan_ms", C.c_double), ("batch_ms", C.c_double), ("count_launches", C.c_uint64),
                 ("select_launches", C.c_uint64), ("render_launches", C.c_uint64), ("plan_launches", C.c_uint64),
-                ("batch_launches", C.c_uint64)]
+                ("batch_launches", C.c_uint64), ("cast_ms", C.c_double), ("voxel_ms", C.c_double),
+                ("cast_launches", C.c_uint64), ("voxel_launches", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -82,7 +83,9 @@ class KernelTimes(C.Structure):
 class EvalStats(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("rays", "dda_steps", "unknown_visits", "samples", "ancestor_tests",
                                           "depth_reads", "render_rays", "render_steps", "count_launches",
-                                          "render_launches")]
+                                          "render_launches", "cast_rays", "cast_steps", "cast_jumps",
+                                          "voxel_candidates", "voxel_unknown", "visit_tests", "owned_samples",
+                                          "voxel_ancestor_tests", "voxel_depth_reads")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -156,6 +159,7 @@ def lib():
                 "mig_last_error": (C.c_char_p, []),
                 "mig_build_flags": (i, []),
                 "mig_probe_gather": (st, [p, C.c_uint64, i, p]),
+                "mig_ctx_set_count_kernel": (st, [p, i, C.c_uint64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name, None)
@@ -245,6 +249,11 @@ class Context:
         t = TileConfig()
         check(lib().mig_batch_get_tiles(self.h, C.byref(t)))
         return (t.tile_w, t.tile_h, t.ctas_per_sm, t.engine)
+
+    def set_count_kernel(self, ray_by_ray=False, steps_budget_bytes=0):
+        """mig_ctx_set_count_kernel: False = owned-voxel counting (default), True = ray by ray;
+        steps_budget_bytes bounds the owned-voxel step-count buffer (0 = the default)."""
+        check(lib().mig_ctx_set_count_kernel(self.h, 1 if ray_by_ray else 0, int(steps_budget_bytes)))
 
     def profile(self, enable=True):
         check(lib().mig_ctx_profile(self.h, 1 if enable else 0))

@@ -11,6 +11,7 @@
 #include "kernels.h"
 #include "mig_impl.h"
 #include "pano.h"
+#include "voxcount.h"
 
 namespace mig {
 
@@ -155,9 +156,31 @@ void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int co
         const int pitems = Ld * p.pano_A;
         launch_pano_count(p, std::max(1, std::min((pitems + 7) / 8, ctx->num_sms * ctx->pano_ctas)), s);
         launch_pano_window(p, std::max(1, std::min((Ld * p.K + 255) / 256, 1024)), s);
+    } else if (p.steps) {
+        launch_vox_level(p, (long long)Ld * p.K, ctx->num_sms, ctx->vox_ctas, s);
     } else {
         launch_count(p, std::max(1, std::min((items + 7) / 8, count_cap)), s);
     }
+}
+
+void launch_level_count_timed(mig_ctx *ctx, const LevelParams &p, int Ld, int count_cap) {
+    if (!p.steps || p.mode == MIG_MODE_INTERVAL || p.mode == MIG_MODE_PANORAMIC) {
+        timed_launch(ctx, kProfCount, [&] { launch_level_count(ctx, p, Ld, count_cap, ctx->stream); });
+        return;
+    }
+    const long long pairs = (long long)Ld * p.K;
+    for (long long q0 = 0; q0 < pairs; q0 += p.steps_cap) {
+        LevelParams c = p;
+        c.q0 = (int)q0;
+        c.q1 = (int)std::min<long long>(pairs, q0 + p.steps_cap);
+        timed_launch(ctx, kProfCast, [&] { launch_cast_chunk(c, ctx->num_sms, ctx->stream); });
+        timed_launch(ctx, kProfVoxel, [&] { launch_voxel_chunk(c, ctx->num_sms, ctx->vox_ctas, ctx->stream); });
+    }
+}
+
+int steps_cap_for(const mig_ctx *ctx, int Lmax, int K, int W, int H, int mode) {
+    if (ctx->ray_count || mode == MIG_MODE_INTERVAL || mode == MIG_MODE_PANORAMIC) return 0;
+    return (int)steps_pairs((long long)std::max(1, Lmax) * K, W, H, ctx->steps_budget);
 }
 
 void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a) {
@@ -274,6 +297,8 @@ mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocat
     ctx->count_ctas = count_ctas_per_sm();
     ctx->interval_ctas = count_interval_ctas_per_sm();
     ctx->pano_ctas = pano_ctas_per_sm();
+    ctx->vox_ctas = vox_ctas_per_sm();
+    ctx->steps_budget = kStepsBudget;
     ctx->d_err = (int32_t *)ctx->alloc.alloc(256, ctx->stream);
     if (!ctx->d_err) return fail(MIG_ENOMEM, "ctx_create: allocation failed");
     MIG_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream));
@@ -332,6 +357,14 @@ mig_status mig_ctx_sync(mig_ctx *ctx) {
     return MIG_OK;
 }
 
+mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int ray_by_ray, uint64_t steps_budget_bytes) {
+    if (!ctx) return fail(MIG_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->ray_count = ray_by_ray != 0;
+    ctx->steps_budget = steps_budget_bytes ? (size_t)steps_budget_bytes : kStepsBudget;
+    return MIG_OK;
+}
+
 mig_status mig_ctx_profile(mig_ctx *ctx, int enable) {
     if (!ctx) return fail(MIG_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -362,6 +395,10 @@ mig_status mig_ctx_profile_read(mig_ctx *ctx, mig_kernel_times *out) {
     out->render_launches = ctx->prof.launches[kProfRender];
     out->plan_launches = ctx->prof.launches[kProfPlan];
     out->batch_launches = ctx->prof.launches[kProfBatch];
+    out->cast_ms = ctx->prof.ms[kProfCast];
+    out->voxel_ms = ctx->prof.ms[kProfVoxel];
+    out->cast_launches = ctx->prof.launches[kProfCast];
+    out->voxel_launches = ctx->prof.launches[kProfVoxel];
     for (int k = 0; k < kProfKinds; ++k) {
         ctx->prof.ms[k] = 0;
         ctx->prof.launches[k] = 0;
@@ -403,7 +440,7 @@ mig_status mig_map_create(mig_ctx *ctx, int nx, int ny, int nz, float voxel_size
             return fail(MIG_ENOMEM, "map_create: staging allocation failed");
         }
         MIG_CUDA_TRY(cudaMemcpyAsync(tmp, host_voxels, nvox, cudaMemcpyHostToDevice, ctx->stream));
-        launch_map_scatter(m->d_grid, m->nx, m->ny, m->nbx, m->nby, tmp, 0, 0, 0, nx, ny, nz, ctx->stream);
+        launch_map_scatter(m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby, tmp, 0, 0, 0, nx, ny, nz, ctx->stream);
         MIG_CUDA_TRY(cudaGetLastError());
         ctx->alloc.free(tmp, nvox, ctx->stream);
     }
@@ -425,7 +462,7 @@ mig_status mig_map_update(mig_map *m, int x0, int y0, int z0, int dx, int dy, in
     uint8_t *tmp = (uint8_t *)ctx->alloc.alloc(nvox, ctx->stream);
     if (!tmp) return fail(MIG_ENOMEM, "map_update: staging allocation failed");
     MIG_CUDA_TRY(cudaMemcpyAsync(tmp, host_voxels, nvox, cudaMemcpyHostToDevice, ctx->stream));
-    launch_map_scatter(m->d_grid, m->nx, m->ny, m->nbx, m->nby, tmp, x0, y0, z0, dx, dy, dz, ctx->stream);
+    launch_map_scatter(m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby, tmp, x0, y0, z0, dx, dy, dz, ctx->stream);
     MIG_CUDA_TRY(cudaGetLastError());
     ctx->alloc.free(tmp, nvox, ctx->stream);
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // the host buffer may be reused on return
@@ -526,8 +563,16 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     const size_t o_cnt = cv.take<int32_t>((size_t)n * K * 2);
     const size_t o_work = cv.take<int32_t>(L);
     const size_t o_arena = cv.take<uint32_t>((size_t)std::max(1, plan.n_internal) * WH);
-    const size_t o_stats = cv.take<unsigned long long>(8);
+    const size_t o_stats = cv.take<unsigned long long>(kStatsCounters);
     const size_t o_pcnt = cv.take<int32_t>(pano ? (size_t)n * cam->pano_A * 2 : 1);
+    int Lmax = 1;
+    for (int d = 0; d < L; ++d) Lmax = std::max(Lmax, plan.level_off[d + 1] - plan.level_off[d]);
+    const int steps_cap = steps_cap_for(ctx, Lmax, K, cam->W, cam->H, mode);
+    const size_t o_steps = cv.take<uint16_t>(std::max<size_t>(1, (size_t)steps_cap * WH));
+    // instrumented pass: the ray-by-ray count kernel is re-run into scratch counters afterwards,
+    // for the method's own work counts (rays, DDA steps, owner tests) and as a cross-check
+    const bool rerun = stats && steps_cap > 0;
+    const size_t o_cnt2 = cv.take<int32_t>(rerun ? (size_t)n * K * 2 + L : 1);
     char *dev = nullptr;
     st = ctx_workspace(ctx, cv.off, (void **)&dev);
     if (st != MIG_OK) return st;
@@ -569,9 +614,11 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     p.bounds_err = ctx->d_err + 16;  // checked build: out-of-buffer indices are recorded here
     MIG_CUDA_TRY(cudaMemsetAsync(p.bounds_err, 0, 4, ctx->stream));
 #endif
+    p.steps = steps_cap ? (uint16_t *)(dev + o_steps) : nullptr;
+    p.steps_cap = steps_cap;
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
-        MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, 64, ctx->stream));
+        MIG_CUDA_TRY(cudaMemsetAsync(p.stats, 0, kStatsCounters * sizeof(unsigned long long), ctx->stream));
     }
     const int cap = ctx->num_sms * 16;
     const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
@@ -579,7 +626,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
         const int Ld = plan.level_off[d + 1] - plan.level_off[d];
-        timed_launch(ctx, kProfCount, [&] { launch_level_count(ctx, p, Ld, count_cap, ctx->stream); });
+        launch_level_count_timed(ctx, p, Ld, count_cap);
         timed_launch(ctx, kProfSelect,
                      [&] { launch_select(p, std::max(1, std::min((Ld + 127) / 128, 1024)), ctx->stream); });
         const int ritems = plan.level_int[d] * render_tiles(p.W, p.H);
@@ -587,12 +634,28 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         n_count++;
         n_render += ritems > 0;
     }
-    unsigned long long st8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (stats) MIG_CUDA_TRY(cudaMemcpyAsync(st8, p.stats, 64, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int32_t> cnt_rerun;
+    if (rerun) {
+        LevelParams r = p;
+        r.steps = nullptr;
+        r.cnt = (int32_t *)(dev + o_cnt2);
+        r.work = r.cnt + (size_t)n * K * 2;
+        MIG_CUDA_TRY(cudaMemsetAsync(r.cnt, 0, ((size_t)n * K * 2 + L) * 4, ctx->stream));
+        for (int d = 0; d < L; ++d) {
+            r.lvl = d;
+            launch_level_count(ctx, r, plan.level_off[d + 1] - plan.level_off[d], count_cap, ctx->stream);
+        }
+        cnt_rerun.resize((size_t)n * K * 2);
+        MIG_CUDA_TRY(cudaMemcpyAsync(cnt_rerun.data(), r.cnt, cnt_rerun.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    unsigned long long st8[kStatsCounters] = {};
+    if (stats)
+        MIG_CUDA_TRY(cudaMemcpyAsync(st8, p.stats, sizeof(st8), cudaMemcpyDeviceToHost, ctx->stream));
     MIG_CUDA_TRY(cudaGetLastError());
     MIG_CUDA_TRY(cudaMemcpyAsync(host, p.out_abs, 3 * (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<int32_t> cnt_h;
-    if (opts && (opts->counts_abs || opts->counts_marg)) {
+    if (rerun) cnt_h.resize((size_t)n * K * 2);
+    if (rerun || (opts && (opts->counts_abs || opts->counts_marg))) {
         cnt_h.resize((size_t)n * K * 2);
         MIG_CUDA_TRY(cudaMemcpyAsync(cnt_h.data(), p.cnt, cnt_h.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
     }
@@ -607,7 +670,9 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     std::memcpy(abs_gain, host, (size_t)n * 4);
     std::memcpy(marg_gain, host + (size_t)n * 4, (size_t)n * 4);
     std::memcpy(best_yaw, host + (size_t)n * 8, (size_t)n * 4);
-    if (!cnt_h.empty()) {
+    if (rerun && cnt_h != cnt_rerun)
+        return fail(MIG_ECUDA, "instrumented pass: the owned-voxel and ray-by-ray counts differ");
+    if (!cnt_h.empty() && opts) {
         for (size_t i = 0; i < (size_t)n * K; ++i) {
             if (opts->counts_abs) opts->counts_abs[i] = cnt_h[2 * i];
             if (opts->counts_marg) opts->counts_marg[i] = cnt_h[2 * i + 1];
@@ -624,6 +689,15 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         stats->render_steps = st8[7];
         stats->count_launches = n_count;
         stats->render_launches = n_render;
+        stats->cast_rays = st8[8];
+        stats->cast_steps = st8[9];
+        stats->cast_jumps = st8[10];
+        stats->voxel_candidates = st8[11];
+        stats->voxel_unknown = st8[12];
+        stats->visit_tests = st8[13];
+        stats->owned_samples = st8[14];
+        stats->voxel_ancestor_tests = st8[15];
+        stats->voxel_depth_reads = st8[16];
     }
     return MIG_OK;
 }
@@ -675,6 +749,10 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     const size_t o_anc = cv.take<int32_t>(std::max<size_t>(1, (size_t)n * max_depth)), o_node = cv.take<int4>(n);
     const size_t o_sel = cv.take<int32_t>(n);
     const size_t o_arena = cv.take<uint32_t>((size_t)n * WH);
+    // level sizes are known on the device only: the step-count buffer is sized for n nodes (its
+    // chunks beyond a level's pairs return at once)
+    const int steps_cap = steps_cap_for(ctx, n, K, cam->W, cam->H, MIG_MODE_MARGINAL);
+    const size_t o_steps = cv.take<uint16_t>(std::max<size_t>(1, (size_t)steps_cap * WH));
     char *dev = nullptr;
     st = ctx_workspace(ctx, cv.off, (void **)&dev);
     if (st != MIG_OK) return st;
@@ -726,12 +804,14 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     p.arena = (uint32_t *)(dev + o_arena);
     p.mode = MIG_MODE_MARGINAL;
     p.max_anc = std::max(1, max_depth);
+    p.steps = steps_cap ? (uint16_t *)(dev + o_steps) : nullptr;
+    p.steps_cap = steps_cap;
     const int cap = ctx->num_sms * 16;
     const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
-        timed_launch(ctx, kProfCount, [&] { launch_count(p, count_cap, ctx->stream); });
+        launch_level_count_timed(ctx, p, n, count_cap);
         timed_launch(ctx, kProfSelect, [&] { launch_select(p, sel_grid, ctx->stream); });
         timed_launch(ctx, kProfRender, [&] { launch_render(p, cap, ctx->stream); });
     }

@@ -562,6 +562,25 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         to[t].arena = cv.take(4 * (size_t)std::max(1, items[t].plan.n_internal) * items[t].cam->W * items[t].cam->H);
         to[t].pcnt = items[t].mode == MIG_MODE_PANORAMIC ? cv.take(8 * (size_t)items[t].plan.n * items[t].cam->pano_A) : 0;
     }
+    // longest trees first, round-robin over the stream pool; the trees of one stream run one after
+    // another, so each stream has one step-count buffer for the owned-voxel count
+    const int S = std::min(T, (int)mig_ctx::Batch::kPool);
+    std::vector<int> order(T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return items[a].plan.n > items[c].plan.n; });
+    std::vector<int> steps_cap(T, 0);
+    std::vector<size_t> stream_steps(S, 0);
+    for (int oi = 0; oi < T; ++oi) {
+        const int t = order[oi];
+        const HostPlan &pl = items[t].plan;
+        int Lmax = 1;
+        for (int d = 0; d <= pl.max_depth; ++d) Lmax = std::max(Lmax, pl.level_off[d + 1] - pl.level_off[d]);
+        steps_cap[t] = steps_cap_for(ctx, Lmax, items[t].cam->K, items[t].cam->W, items[t].cam->H, items[t].mode);
+        stream_steps[oi % S] =
+            std::max(stream_steps[oi % S], (size_t)steps_cap[t] * items[t].cam->W * items[t].cam->H * sizeof(uint16_t));
+    }
+    std::vector<size_t> o_steps(S);
+    for (int i = 0; i < S; ++i) o_steps[i] = cv.take(std::max<size_t>(stream_steps[i], 1));
     char *dev = nullptr;
     mig_status st = ctx_workspace(ctx, cv.off, (void **)&dev);
     if (st != MIG_OK) return st;
@@ -613,9 +632,13 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         if (it.mode == MIG_MODE_PANORAMIC) set_pano_params(p, it.cam, (int32_t *)(dev + to[t].pcnt));
         lp[t] = p;
     }
+    for (int oi = 0; oi < T; ++oi) {
+        const int t = order[oi];
+        lp[t].steps = steps_cap[t] ? (uint16_t *)(dev + o_steps[oi % S]) : nullptr;
+        lp[t].steps_cap = steps_cap[t];
+    }
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();
     mig_ctx::Batch *B = ctx->batch;
-    const int S = std::min(T, (int)B->kPool);
     for (int i = (int)B->pool.size(); i < S; ++i) {
         cudaStream_t s = nullptr;
         cudaEvent_t e = nullptr;
@@ -625,10 +648,6 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         B->join.push_back(e);
     }
     if (!B->fork) MIG_CUDA_TRY(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
-    // longest trees first, round-robin over the pool
-    std::vector<int> order(T);
-    for (int t = 0; t < T; ++t) order[t] = t;
-    std::sort(order.begin(), order.end(), [&](int a, int c) { return items[a].plan.n > items[c].plan.n; });
     cudaStream_t s0 = ctx->stream;
     const int cap = ctx->num_sms * 16;
     const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));

@@ -11,6 +11,8 @@
 #include "dev_path.cuh"
 #include "kernels.h"
 #include "mig.h"
+#include "voxcount.cuh"
+#include "voxcount.h"
 
 namespace mig {
 
@@ -206,7 +208,8 @@ size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz) {
     *nby = (ny + 7) / 8;
     *nbz = (nz + 7) / 8;
 #if MIG_LAYOUT == 1
-    return (size_t)nx * ny * nz;
+    // voxel codes, then (256-byte aligned) one occupancy byte per 8x8x8 brick
+    return bocc_offset(nx, ny, nz) + (size_t)*nbx * *nby * *nbz;
 #else
     return (size_t)*nbx * *nby * *nbz * 512;
 #endif
@@ -229,11 +232,16 @@ void launch_render(const LevelParams &p, int grid, cudaStream_t s) {
 }
 
 int render_tiles(int W, int H) { return ((W + 15) / 16) * ((H + 15) / 16); }
-void launch_map_scatter(uint8_t *bricks, int nx, int ny, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0,
-                        int dx, int dy, int dz, cudaStream_t s) {
+void launch_map_scatter(uint8_t *bricks, int nx, int ny, int nz, int nbx, int nby, const uint8_t *box, int x0, int y0,
+                        int z0, int dx, int dy, int dz, cudaStream_t s) {
     const size_t total = (size_t)dx * dy * dz;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
     map_scatter_kernel<<<grid, 256, 0, s>>>(bricks, nx, ny, nbx, nby, box, x0, y0, z0, dx, dy, dz);
+#if MIG_LAYOUT == 1
+    launch_bocc(bricks, nx, ny, nz, x0, y0, z0, dx, dy, dz, s);  // the occupancy bytes of the bricks it touched
+#else
+    (void)nz;
+#endif
 }
 void launch_map_gather(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz, cudaStream_t s) {
     const size_t total = (size_t)nx * ny * nz;

@@ -7,6 +7,8 @@
 
 namespace mig {
 
+constexpr int kStatsCounters = 20;
+
 struct GridView {
     const uint8_t *g;  // voxel codes in the traversal layout (x-fastest rows or 8x8x8 bricks)
     int nx, ny, nz;
@@ -35,7 +37,7 @@ struct LevelParams {
     int32_t *out_abs, *out_marg, *out_yaw;  // device, n
     int mode;                   // mig_mode
     int lvl;
-    unsigned long long *stats;  // NULL, or 8 counters (instrumented pass)
+    unsigned long long *stats;  // NULL, or kStatsCounters counters (instrumented pass)
     int max_anc;                // ancestor records per warp (>= the deepest node's depth, <= 64)
     // panoramic mode: A wedges ("columns") of `pano_step` per yaw bin, Wc columns per yaw window
     int pano_A, pano_Wc, pano_step;
@@ -47,6 +49,11 @@ struct LevelParams {
     // not recorded) and the access is skipped; arena_slots = depth buffers in the arena (0: unchecked)
     int32_t *bounds_err;
     int arena_slots;
+    // owned-voxel count (voxcount.cu): per-ray DDA step counts of a chunk of (node, yaw) pairs
+    // [q0, q1) of the level, steps_cap pairs of W * H each; NULL = the ray-by-ray count kernel
+    uint16_t *steps;
+    int steps_cap;
+    int q0, q1;
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);
@@ -54,8 +61,10 @@ int count_ctas_per_sm();  // resident CTAs per SM of the count kernel
 void launch_select(const LevelParams &p, int grid, cudaStream_t s);
 void launch_render(const LevelParams &p, int grid, cudaStream_t s);
 int render_tiles(int W, int H);  // 16x16 pixel tiles of the render pass
-void launch_map_scatter(uint8_t *bricks, int nx, int ny, int nbx, int nby, const uint8_t *box, int x0, int y0, int z0,
-                        int dx, int dy, int dz, cudaStream_t s);
+// Writes a box of voxel codes into a grid of nx * ny * nz and refreshes the brick occupancy bytes
+// of the bricks it touches.
+void launch_map_scatter(uint8_t *bricks, int nx, int ny, int nz, int nbx, int nby, const uint8_t *box, int x0, int y0,
+                        int z0, int dx, int dy, int dz, cudaStream_t s);
 // device bytes of an nx*ny*nz grid in the traversal layout (and its brick counts)
 size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz);
 void launch_map_gather(const uint8_t *bricks, int nbx, int nby, uint8_t *lin, int nx, int ny, int nz, cudaStream_t s);

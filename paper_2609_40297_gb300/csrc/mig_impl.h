@@ -86,7 +86,7 @@ mig_status plan_build(int n, const int32_t *parent, const float *pos, const floa
                       const int dims[3], HostPlan &p);
 
 // CUDA-event timing of the library's own launches (mig_ctx_profile).
-enum ProfKind { kProfCount = 0, kProfSelect, kProfRender, kProfPlan, kProfBatch, kProfKinds };
+enum ProfKind { kProfCount = 0, kProfSelect, kProfRender, kProfPlan, kProfBatch, kProfCast, kProfVoxel, kProfKinds };
 struct Profiler {
     bool on = false;
     struct Pair {
@@ -95,8 +95,8 @@ struct Profiler {
     };
     std::vector<Pair> pending;
     std::vector<cudaEvent_t> pool;
-    double ms[kProfKinds] = {0, 0, 0, 0, 0};
-    uint64_t launches[kProfKinds] = {0, 0, 0, 0, 0};
+    double ms[kProfKinds] = {};
+    uint64_t launches[kProfKinds] = {};
 };
 
 }  // namespace mig
@@ -110,6 +110,9 @@ struct mig_ctx {
     int count_ctas = 1;        // resident count-kernel CTAs per SM
     int interval_ctas = 1;     // resident interval-mode count CTAs per SM
     int pano_ctas = 1;         // resident panoramic count CTAs per SM
+    int vox_ctas = 1;          // resident owned-voxel count CTAs per SM
+    bool ray_count = false;    // count with the ray-by-ray kernel instead of the owned-voxel kernels
+    size_t steps_budget = 0;   // owned-voxel step-count buffer per evaluation (bytes; set at creation)
     std::vector<std::unique_ptr<mig::Camera>> cameras;
     mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
     void *pinned = nullptr;  // pinned host staging
@@ -146,8 +149,16 @@ mig_status ctx_pano(mig_ctx *ctx, const Camera *cam);
 // Panoramic level parameters from the camera's tables; pcnt = n * A * 2 int32 of workspace.
 void set_pano_params(LevelParams &p, const Camera *cam, int32_t *pcnt);
 // One level's count pass for p.mode: the sample, interval or panoramic kernels (Ld = nodes of
-// the level). The panoramic mode also runs its window sums, so launch_select may follow.
+// the level, or an upper bound of it for the sample modes' owned-voxel kernels, which read the
+// level's size on the device). The sample modes use the owned-voxel kernels when p.steps is set,
+// else the ray-by-ray count kernel. The panoramic mode also runs its window sums, so
+// launch_select may follow.
 void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int count_cap, cudaStream_t s);
+// The same on the context stream, each launch timed under its own kind (mig_ctx_profile).
+void launch_level_count_timed(mig_ctx *ctx, const LevelParams &p, int Ld, int count_cap);
+// (node, yaw) pairs per owned-voxel chunk for a tree whose widest level has Lmax nodes (0 when the
+// context counts ray by ray); the step-count buffer holds steps_cap * W * H uint16.
+int steps_cap_for(const mig_ctx *ctx, int Lmax, int K, int W, int H, int mode);
 // records an event pair around launch() on the context stream when profiling is on
 void prof_begin(mig_ctx *ctx, int kind, cudaEvent_t *a);
 void prof_end(mig_ctx *ctx, int kind, cudaEvent_t a);
@@ -162,7 +173,8 @@ struct NvtxRange {
 
 template <class F>
 inline void timed_launch(mig_ctx *ctx, int kind, F &&launch) {
-    static const char *const kNames[kProfKinds] = {"mig count", "mig select", "mig render", "mig plan", "mig batch"};
+    static const char *const kNames[kProfKinds] = {"mig count", "mig select", "mig render", "mig plan",
+                                                   "mig batch", "mig cast",   "mig voxel"};
     NvtxRange range(kNames[kind]);
     cudaEvent_t a = nullptr;
     prof_begin(ctx, kind, &a);

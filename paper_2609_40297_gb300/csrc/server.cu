@@ -46,6 +46,7 @@ struct Request {
     mig_sensor sensor{};
     int mode = 0;
     HostPlan plan;
+    int steps_cap = 0;  // owned-voxel count: (node, yaw) pairs per chunk (0 = ray by ray)
     int32_t *out_abs = nullptr, *out_marg = nullptr, *out_yaw = nullptr;
     const Camera *cam = nullptr;
     // device state while in flight
@@ -120,6 +121,7 @@ size_t request_bytes(const Request &r) {
     cv.take(12 * n);
     cv.take(4 * n);
     cv.take(4 * std::max(1, pl.n_internal) * WH);
+    cv.take(std::max<size_t>(1, (size_t)r.steps_cap * WH * sizeof(uint16_t)));
     return cv.off;
 }
 
@@ -154,6 +156,7 @@ mig_status admit(mig_server *s, Request &r) {
     const size_t o_out = cv.take(12 * (size_t)n), o_sel = cv.take(4 * (size_t)n);
     const size_t o_arena = cv.take(4 * (size_t)std::max(1, pl.n_internal) * WH);
     const size_t o_pcnt = pano ? cv.take(8 * (size_t)n * r.cam->pano_A) : 0;
+    const size_t o_steps = cv.take(std::max<size_t>(1, (size_t)r.steps_cap * WH * sizeof(uint16_t)));
     r.dev_bytes = cv.off;
     r.dev = (char *)ctx->alloc.alloc(r.dev_bytes, ctx->stream);
     if (!r.dev) return fail(MIG_ENOMEM, "server: request allocation failed");
@@ -213,6 +216,8 @@ mig_status admit(mig_server *s, Request &r) {
     p.stats = nullptr;
     p.max_anc = std::max(1, pl.max_depth);
     if (pano) set_pano_params(p, r.cam, (int32_t *)(r.dev + o_pcnt));
+    p.steps = r.steps_cap ? (uint16_t *)(r.dev + o_steps) : nullptr;
+    p.steps_cap = r.steps_cap;
     r.level = 0;
     return MIG_OK;
 }
@@ -244,7 +249,7 @@ mig_status apply_update(mig_server *s, Update &u) {
     uint8_t *tmp = (uint8_t *)ctx->alloc.alloc(nv, ctx->stream);
     if (!tmp) return fail(MIG_ENOMEM, "server: update staging allocation failed");
     MIG_CUDA_TRY(cudaMemcpyAsync(tmp, u.voxels.data(), nv, cudaMemcpyHostToDevice, ctx->stream));
-    launch_map_scatter(m->d_grid, m->nx, m->ny, m->nbx, m->nby, tmp, u.x0, u.y0, u.z0, u.dx, u.dy, u.dz, ctx->stream);
+    launch_map_scatter(m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby, tmp, u.x0, u.y0, u.z0, u.dx, u.dy, u.dz, ctx->stream);
     MIG_CUDA_TRY(cudaGetLastError());
     ctx->alloc.free(tmp, nv, ctx->stream);
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // the host voxels are freed with the update
@@ -428,6 +433,12 @@ extern "C" mig_status mig_server_submit(mig_server *s, const mig_tree_desc *d, u
     r->map = d->map;
     r->sensor = d->sensor;
     r->mode = d->mode;
+    {
+        int Lmax = 1;
+        for (int lv = 0; lv <= r->plan.max_depth; ++lv)
+            Lmax = std::max(Lmax, r->plan.level_off[lv + 1] - r->plan.level_off[lv]);
+        r->steps_cap = steps_cap_for(s->ctx, Lmax, d->sensor.yaw_bins, d->sensor.width, d->sensor.height, d->mode);
+    }
     r->out_abs = d->abs_gain;
     r->out_marg = d->marg_gain;
     r->out_yaw = d->best_yaw;

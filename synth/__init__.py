@@ -552,6 +552,28 @@ def serving_trace(seed=505, n_maps=4, robots_per_map=4, rate_hz=20.0, duration_s
     return maps, pools, events, SENSOR_PAPER
 
 
+def serving_requests(seed=505, duration_s=30.0, rate_hz=20.0, update_seed=77, n_first=None):
+    """The serving workload as a request sequence: serving_trace's maps, tree pools and Poisson
+    events, plus the map update that precedes each request (a box of 10 % of the voxels,
+    re-labelled from ground truth, drawn with its own seeded generator). n_first keeps the first
+    requests only. Returns (maps, pools, events, sensor, updates); updates[i] =
+    ((x0, y0, z0, dx, dy, dz), voxels[dz, dy, dx]) for events[i] = (t, robot, map, tree)."""
+    maps, pools, events, sensor = serving_trace(seed=seed, duration_s=duration_s, rate_hz=rate_hz)
+    if n_first is not None:
+        events = events[:n_first]
+    rng = np.random.default_rng(update_seed)
+    updates = [map_update_box(rng, maps[mi], 0.10) for (_, _, mi, _) in events]
+    return maps, pools, events, sensor, updates
+
+
+def apply_update(grid, update):
+    """The grid (nz, ny, nx) after one map update ((x0, y0, z0, dx, dy, dz), voxels), as a copy."""
+    (x0, y0, z0, dx, dy, dz), vox = update
+    g = grid.copy()
+    g[z0:z0 + dz, y0:y0 + dy, x0:x0 + dx] = vox
+    return g
+
+
 def tiny_tree(positions, parents):
     return Tree(parent=np.asarray(parents, np.int32), pos=np.asarray(positions, np.float32))
 

@@ -1,21 +1,29 @@
 """Benchmark: marginal-gain throughput of the GB300 path on the seeded synthetic workloads.
 
-Default (N=1): the paper-scale workload, 400x400x100 voxels at 0.1 m, a 500-node RRT of depth
-<= 10, 160x120 rays, K = 16 yaws, 6 m range. One step = one whole-tree evaluation (every node,
-yaw and ray: count, ancestor test, yaw argmax, depth render).
-  value = marginal-gain rays per second = nodes * K * W * H / device time, inputs resident in HBM,
-          timed with CUDA events on the library's stream, L2 flushed between steps;
-  e2e   = the same metric through the public host-array call (mig_tree_eval), host<->device
-          copies inside the timed region.
-Multi-GPU (torchrun, one rank per GPU): replicas only. Every rank evaluates its own seeded tree
-per step, no collective on the data path; value = all ranks' rays / max-over-ranks time.
+Default (N=1), one JSON line:
+- headline: the large workload, 800x800x200 voxels at 0.05 m, a 2000-node RRT of depth <= 15,
+  320x240 rays, K = 36 yaws, 8 m range. One step = one whole-tree evaluation (every node, yaw and
+  ray: count, ancestor test, yaw argmax, depth render) through the device-resident call.
+    value = marginal-gain rays per second = nodes * K * W * H / device time, inputs resident in HBM,
+            CUDA events on the library's stream, L2 flushed between steps;
+    e2e   = the same metric through the public host-array call (mig_tree_eval), host<->device copies
+            inside the timed region;
+- paper_scale: the same measurement on the 400x400x100, 500-node, 160x120, K = 16 workload;
+- batched: 64 trees on 64 maps (50-2000 nodes, ray grids 64x48 ... 320x240) in one batched call
+  against 64 sequential plain calls, repeated, with the spread;
+- serving: 16 robots on 4 maps with Poisson arrivals through the continuous-batching server against
+  the same requests as lone calls: at the specified 20 Hz per robot (far above capacity: the queue
+  grows) and at a load the GPU can keep up with; p50 / p99 latency and replans/s;
+- roofline of the dominant kernel, cpu_baseline (the CPU oracle on this host's cores, on a bounded
+  sample of the large workload), the gap of the depth-buffer gain to the exact one.
+Multi-GPU (torchrun, one rank per GPU): replicas only. Every rank evaluates its own seeded tree per
+step, no collective on the data path; value = all ranks' rays / max-over-ranks time.
 
---impl reference: the CPU oracle (the plain C restatement of the method) timed on this host's
-cores on a bounded sample of the same workload, same metric and unit.
---workload batched | serving | large | tiny: the other configurations (64 trees batched against 64
-plain calls; the serving loop with p50/p99 latency; the 800x800x200 large workload; the tiny one).
-The single-tree workloads also time every gain mode through the public call (`modes`) and, from the
-oracle, report each mode's gap to the exact marginal gain.
+--impl reference: the CPU oracle (the plain C restatement of the method) timed on this host's cores
+on a bounded sample of the same workload, same metric and unit.
+--workload large | paper_scale | tiny | batched | batched_small | serving: one part alone (the
+single-tree workloads also time every gain mode through the public call and report each mode's gap
+to the exact marginal gain from the oracle).
 """
 from __future__ import annotations
 
@@ -39,6 +47,8 @@ if ROOT not in sys.path:
 
 METRIC = "marginal-gain rays/s & replans/s; p50/p99 replan latency, batched vs plain"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+DTYPE = "int32/int64 fixed point (u8 map)"
+DATA = "synthetic (seeded; stands in for the paper's Gazebo worlds)"
 
 
 # ----------------------------------------------------------------------------- utilities
@@ -108,48 +118,6 @@ def l2_flush_buffer(torch, dev):
     return torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
 
 
-def kernel_source_hash():
-    """Hash of the count kernel's code (its source files with comments and blank lines removed), so
-    that an ncu summary stays tied to the code it measured, not to its comments."""
-    h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.h", "dev_path.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f)) as fh:
-            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        lines = [ln.split("//", 1)[0].rstrip() for ln in txt.splitlines()]
-        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
-    return h.hexdigest()[:16]
-
-
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel
-    source (the summary records the source hash); else None."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    if not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not mh or not mt or mh.group(1) != kernel_source_hash():
-        return None
-    return float(mt.group(1))
-
-
-# Algorithmic integer operations per unit of work, from the fixed-point specification:
-#  - a DDA step: 6 cross products, 3 comparisons, axis choice (2), step budget check and decrement (2),
-#    face distance, voxel index and address updates (3), voxel load and code test (2) = 18;
-#  - an owner test: offsets (3), Z and U and V (3 x 5), pixel-slab products (4) and comparisons (4) = 26;
-#  - an ancestor projection: offsets (3), Z, U, V (15), image bounds (4), pixel floors (4), depth read
-#    and comparison (2), float estimate (2) = 30.
-OPS_PER_STEP, OPS_PER_OWNER_TEST, OPS_PER_ANCESTOR_TEST = 18, 26, 30
-
-
-def issue_peak_ops(sm_clock_mhz=None):
-    """Integer issue ceiling of a GB300: 152 SMs x 4 schedulers x 32 lanes per clock, at the SM clock
-    seen under load (else the 2070 MHz maximum)."""
-    mhz = sm_clock_mhz or 2070.0
-    return 152 * 4 * 32 * mhz * 1e6
-
-
 def max_over_ranks(x, device=None):
     """Largest value over all ranks (a no-op on one process); gloo or NCCL."""
     import torch
@@ -170,7 +138,84 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def spread(xs):
+    xs = [float(x) for x in xs]
+    return {"median": float(np.median(xs)), "min": min(xs), "max": max(xs), "n": len(xs)}
+
+
+# -------------------------------------------------------------------- kernels and roofline
+# Source files whose code (comments and blank lines removed) an ncu summary is tied to.
+KERNEL_SOURCES = {
+    "cast_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
+    "voxel_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
+    "count_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
+    "render_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2609_40297_gb300", "csrc", f)) as fh:
+            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = [ln.split("//", 1)[0].rstrip() for ln in txt.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
+    return h.hexdigest()[:16]
+
+
+def profiled(kernel, workload):
+    """Figures of a committed ncu summary (profiles/<kernel>_<workload>.md) taken on the current
+    kernel source (the summary records the source hash): DRAM bytes per launch scaled to the
+    full launch, and the launch's own algorithmic units (for the scaling); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not mh or mh.group(1) != kernel_source_hash(kernel):
+        return None
+    out = {}
+    for key in ("dram_bytes_per_launch", "issue_active_pct", "threads_per_inst", "l2_hit_pct"):
+        m = re.search(rf"{key}:\s*([0-9.eE+]+)", txt)
+        if m:
+            out[key] = float(m.group(1))
+    return out or None
+
+
+# Algorithmic bytes per unit of work (the survey's per-unit figures, applied to the units each
+# kernel processes): a voxel step or a brick jump reads 1 B; a cast ray reads its 16 B ray-table
+# entry and writes its 2 B step count; an enumerated voxel reads 1 B; a counted sample reads its
+# owner pixel's 2 B step count and 16 B ray entry; an ancestor test that reaches the buffer reads
+# a 4 B depth texel; a rendered pixel writes a 4 B texel.
+def kernel_units(kernel, st):
+    if kernel == "cast_kernel":
+        return (st["cast_steps"] + st["cast_jumps"] + 18 * st["cast_rays"],
+                "voxel steps + brick jumps (1 B each) + cast rays (16 B ray entry + 2 B step count)")
+    if kernel == "voxel_kernel":
+        return (st["voxel_candidates"] + 18 * st["owned_samples"] + 4 * st["voxel_depth_reads"],
+                "enumerated voxels (1 B) + counted samples (2 B step count + 16 B ray entry) + depth reads (4 B)")
+    if kernel == "count_kernel":
+        return (st["dda_steps"] + 4 * st["depth_reads"], "DDA steps (1 B) + depth reads (4 B)")
+    return (st["render_steps"] + 4 * st["render_rays"], "render DDA steps (1 B) + texels written (4 B)")
+
+
+def method_bytes(st):
+    """The ray-by-ray method's own algorithmic bytes per evaluation (the survey's per-unit
+    figures on the method's units: 1 B per DDA step of every ray, 4 B per ancestor depth read,
+    4 B per rendered texel), counted by the instrumented pass."""
+    return st["dda_steps"] + 4 * st["depth_reads"] + 4 * st["render_rays"]
+
+
 # ----------------------------------------------------------------------------- workloads
+WORKLOAD_DESC = {
+    "paper_scale": "paper-scale: 400x400x100 voxels @0.1 m (rooms, 5 prior scans), 500-node RRT depth<=10, "
+                   "160x120 rays, 90x60 deg, 6 m, K=16 yaws",
+    "tiny": "tiny: 64x64x32 @0.2 m, 20-node RRT depth<=4, 36x24 rays, 4 m, K=8",
+    "large": "large: 800x800x200 @0.05 m (Perlin terrain + boxes, 5 prior scans), 2000-node RRT depth<=15, "
+             "320x240 rays, 90x60 deg, 8 m, K=36 yaws",
+}
+
+
 def make_problem(workload, rank):
     import synth
     if workload == "paper_scale":
@@ -182,33 +227,29 @@ def make_problem(workload, rank):
     raise ValueError(workload)
 
 
-WORKLOAD_DESC = {
-    "paper_scale": "paper-scale: 400x400x100 voxels @0.1 m (rooms, 5 prior scans), 500-node RRT depth<=10, "
-                   "160x120 rays, 90x60 deg, 6 m, K=16 yaws",
-    "tiny": "tiny: 64x64x32 @0.2 m, 20-node RRT depth<=4, 36x24 rays, 4 m, K=8",
-    "large": "large: 800x800x200 @0.05 m (Perlin terrain), 2000-node RRT depth<=15, 320x240 rays, 8 m, K=36",
-}
+def init_dist(local):
+    import torch
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    return torch.device("cuda", local)
 
 
-def oracle_sample_mask(tree, max_depth_sample):
-    d = tree.depth()
-    return (d <= max_depth_sample).astype(np.uint8)
-
-
-# ----------------------------------------------------------------------------- our arm
-def run_ours(args):
+# ----------------------------------------------------------------------------- one tree
+def measure_single(workload, steps, warmup, with_modes=False):
+    """Times `steps` whole-tree evaluations of one workload on the device-resident path (after
+    `warmup`), then the host-array path end to end; returns the benchmark's fields."""
     import torch
 
     import paper_2609_40297_gb300 as mig
     import synth
 
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    prob = make_problem(args.workload, rank)
+    dev = init_dist(local)
+    prob = make_problem(workload, rank)
     s = prob.sensor
     n = prob.tree.n
     max_depth = int(prob.tree.depth().max())
@@ -224,10 +265,11 @@ def run_ours(args):
     def step():
         mig.tree_eval_device(m, par, pos, s, max_depth, *outs)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     ctx.sync()
-    # algorithmic work of one step (instrumented pass, untimed)
+    # algorithmic work of one step (instrumented pass, untimed; it re-runs the ray-by-ray count
+    # kernel beside the owned-voxel one for the method's own work counts and checks they agree)
     ref_out, stats = mig.tree_eval_stats(m, prob.tree.parent, prob.tree.pos, s)
     # ---- timed region: K steps, device time per step with CUDA events, L2 flushed between steps
     if ws > 1:
@@ -236,9 +278,9 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     ctx.profile(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
         flush.fill_(i & 0xFF)
         starts[i].record(stream)
         step()
@@ -248,14 +290,16 @@ def run_ours(args):
     ctx.profile(False)
     clocks = sampler.stop()
     ctx.sync()
+    if ws > 1:
+        torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = max_over_ranks(float(sum(step_ms)), dev)
     got = [o.cpu().numpy() for o in outs]
     ok = all(np.array_equal(a, ref_out[k]) for a, k in zip(got, ("abs", "marg", "yaw")))
-    value = ws * rays_per_step * args.steps / (total_ms / 1e3)
+    value = ws * rays_per_step * steps / (total_ms / 1e3)
     # ---- end to end: host arrays through the public call (copies in the timed region)
     e2e_ms = []
-    for i in range(max(3, min(args.steps, 10))):
+    for i in range(max(3, min(steps, 5))):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -263,144 +307,132 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = max_over_ranks(float(np.sum(e2e_ms)), dev)
     e2e_value = ws * rays_per_step * len(e2e_ms) / (e2e_total / 1e3)
-    # ---- the gain modes side by side (Table 2's absolute vs marginal columns, and the paper's
-    # screen-space interval overlap against voxel-centre samples), each through the public host-array
-    # call, outside the timed region: median of 3 after one warm-up (a mode slower than 2 s per call:
-    # that first call alone)
-    modes, yaws = {}, {}
-    if rank == 0 and not args.no_modes:
-        for name, md in (("marginal_samples", mig.MODE_MARGINAL), ("marginal_intervals", mig.MODE_INTERVAL),
-                         ("single_parent", mig.MODE_SINGLE_PARENT), ("absolute", mig.MODE_ABSOLUTE),
-                         ("panoramic", mig.MODE_PANORAMIC)):
-            if md == mig.MODE_PANORAMIC and s.pitch_deg != 0:
-                continue
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
-            first_ms = (time.perf_counter() - t0) * 1e3
-            ts = []
-            for _ in range(3 if first_ms < 2000 else 0):  # slow modes: the first call alone
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
-                ts.append((time.perf_counter() - t0) * 1e3)
-            ms = float(np.median(ts)) if ts else first_ms
-            modes[name] = {"ms_per_replan": ms, "rays_per_s": rays_per_step / (ms / 1e3),
-                           "marg_sum": int(g["marg"].sum()), "abs_sum": int(g["abs"].sum())}
-            if md == mig.MODE_PANORAMIC:
-                modes[name]["note"] = ("rays_per_s counts the pinhole rays the mode stands in for (nodes x K x W x H); "
-                                       "it casts nodes x A x H with A azimuth columns")
-            yaws[name] = g["yaw"]
-        for name in modes:  # how often each mode picks the same viewpoint as voxel-centre samples
-            modes[name]["same_yaw_as_samples"] = float(np.mean(yaws[name] == yaws["marginal_samples"]))
-    # ---- roofline of the dominant kernel (count pass). It is bound by integer issue: achieved =
-    # algorithmic integer operations per launch / average launch time, against the issue ceiling.
-    # The gather roofline (algorithmic voxel + depth bytes against HBM) is reported beside it.
-    count_launches = max(1, int(ktimes["count_launches"]))
-    launches_per_step = count_launches / args.steps
-    avg_launch_s = ktimes["count_ms"] / 1e3 / count_launches
-    alg_ops_launch = (stats["dda_steps"] * OPS_PER_STEP + stats["unknown_visits"] * OPS_PER_OWNER_TEST +
-                      stats["ancestor_tests"] * OPS_PER_ANCESTOR_TEST) / launches_per_step
-    alg_bytes_launch = (stats["dda_steps"] * 1 + stats["depth_reads"] * 4) / launches_per_step
-    achieved_ops = alg_ops_launch / avg_launch_s / 1e9
-    peak_ops = issue_peak_ops((clocks or {}).get("sm_mhz")) / 1e9
+    modes = with_modes and rank == 0 and run_modes(mig, torch, m, prob, rays_per_step) or None
+    # ---- roofline of the dominant kernel: its algorithmic bytes per launch over its average launch
+    # time, against the measured HBM copy bandwidth
+    kms = {k: ktimes[f"{k}_ms"] for k in ("cast", "voxel", "count", "render")}
+    dom = max(kms, key=kms.get)
+    kernel = f"{dom}_kernel"
+    launches = max(1, int(ktimes[f"{dom}_launches"]))
+    lps = launches / steps
+    avg_launch_s = kms[dom] / 1e3 / launches
+    units, unit_desc = kernel_units(kernel, stats)
+    alg_bytes_launch = units / lps
     achieved = alg_bytes_launch / avg_launch_s / 1e9
     peak, peak_kind = load_peaks()
-    # the random-gather ceiling for the count pass's scattered loads, measured here by a probe:
-    # 1-byte loads from a map-sized buffer (L2-resident) and 4-byte loads from an arena-sized one
-    grid_bytes = int(prob.map.grid.size)
-    gp_voxel = mig.probe_gather(ctx, grid_bytes, 1)
-    gp_texel = mig.probe_gather(ctx, max(4096, int(prob.tree.n) * s.width * s.height * 4), 4)
-    gathers_launch = (stats["dda_steps"] + stats["depth_reads"]) / launches_per_step
-    gather_rate = gathers_launch / avg_launch_s
-    gather_peak = (stats["dda_steps"] + stats["depth_reads"]) / (stats["dda_steps"] / gp_voxel + stats["depth_reads"] / gp_texel)
-    traffic = profiled_traffic("count_kernel", args.workload)
+    prof = profiled(kernel, workload)
+    count_pass_ms = (kms["cast"] + kms["voxel"] + kms["count"]) / steps
     n_launches = int(ktimes["count_launches"] + ktimes["select_launches"] + ktimes["render_launches"] +
-                     ktimes["plan_launches"] * 4)
-    res = None
-    if rank == 0:
-        res = {
-            "metric": METRIC,
-            "value": value,
-            "unit": "rays/s",
-            "n_gpus": ws,
-            "steps": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "int32/int64 fixed point (u8 map)",
-            "data": "synthetic (seeded; stands in for the paper's Gazebo worlds)",
-            "config": {"workload": WORKLOAD_DESC[args.workload], "nodes": n, "yaw_bins": s.yaw_bins,
-                       "rays_per_node_yaw": s.width * s.height, "max_depth": max_depth,
-                       "inputs_sha256_16": synth.sha256(prob.map.grid, prob.tree.parent, prob.tree.pos)[:16],
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
-            "replans_per_s": ws * args.steps / (total_ms / 1e3),
-            "nodes_per_s": ws * n * args.steps / (total_ms / 1e3),
-            "replan_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "results_match_host_path": bool(ok),
-            "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": int(n * 16),
-                    "d2h_bytes_per_step": int(n * 12), "ms_per_step": e2e_total / len(e2e_ms)},
-            "gpu_launches": n_launches,
-            "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Gop/s",
-                         "frac": achieved_ops / peak_ops, "traffic": traffic, "kernel": "count_kernel",
-                         "algorithmic_ops_per_launch": alg_ops_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                         "peak_source": "issue ceiling: 152 SMs x 4 schedulers x 32 lanes x the SM clock sampled under load",
-                         "note": f"ops/unit: DDA step {OPS_PER_STEP}, owner test {OPS_PER_OWNER_TEST}, "
-                                 f"ancestor projection {OPS_PER_ANCESTOR_TEST}; traffic = ncu DRAM bytes of one "
-                                 "launch (level 8) when the committed summary matches the kernel source"},
-            "gather_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                                "algorithmic_bytes_per_launch": alg_bytes_launch,
-                                "note": "algorithmic bytes = DDA voxel gathers (1 B) + ancestor depth reads (4 B); "
-                                        "ncu: L2 sector hit 99 %, 3.6 sectors per load request"},
-            "gather_rate_roofline": {"bound": "l2_random_gather", "achieved": gather_rate / 1e9,
-                                     "peak": gather_peak / 1e9, "unit": "Gloads/s", "frac": gather_rate / gather_peak,
-                                     "peak_source": "measured by mig_probe_gather on this GPU (random 1-byte loads from a "
-                                                    f"{grid_bytes >> 20} MiB map-sized buffer: {gp_voxel / 1e9:.0f} G/s; "
-                                                    f"random 4-byte loads from an arena-sized buffer: {gp_texel / 1e9:.0f} G/s), "
-                                                    "weighted by the launch's voxel and depth-texel loads",
-                                     "gathers_per_launch": gathers_launch,
-                                     "note": "the probe's loads are fully random (32 sectors per warp request); the "
-                                             "kernel's neighbouring rays load neighbouring voxels (3.6 sectors per "
-                                             "request and 69 % L1 hits, ncu level 8), so its L2 sector traffic is far "
-                                             "below this ceiling (47.7 G sectors/s under ncu, ~15 %); integer issue "
-                                             "(roofline) is the binding resource"},
-            "modes": modes or None,
-            "work_per_step": stats,
-            "kernel_ms_per_step": {k.replace("_ms", ""): v / args.steps for k, v in ktimes.items() if k.endswith("_ms")},
-            "clocks": clocks,
-        }
+                     ktimes["plan_launches"] * 4 + ktimes["cast_launches"] + ktimes["voxel_launches"])
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    res = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": warmup,
+        "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE, "data": DATA,
+        "config": {"workload": WORKLOAD_DESC[workload], "nodes": n, "yaw_bins": s.yaw_bins,
+                   "rays_per_node_yaw": s.width * s.height, "max_depth": max_depth,
+                   "inputs_sha256_16": synth.sha256(prob.map.grid, prob.tree.parent, prob.tree.pos)[:16],
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
+        "replans_per_s": ws * steps / (total_ms / 1e3),
+        "nodes_per_s": ws * n * steps / (total_ms / 1e3),
+        "replan_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "results_match_host_path": bool(ok),
+        "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": int(n * 16),
+                "d2h_bytes_per_step": int(n * 12), "ms_per_step": e2e_total / len(e2e_ms)},
+        "gpu_launches": n_launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": prof["dram_bytes_per_launch"] if prof and "dram_bytes_per_launch" in prof else None,
+                     "kernel": kernel, "algorithmic_bytes_per_launch": alg_bytes_launch,
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches_per_step": lps,
+                     "units": unit_desc, "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "ncu": prof,
+                     "note": "the kernel is bound by integer issue and L2-served gathers, not by HBM: its data "
+                             "(map, step counts, depth buffers) stays L2-resident between its loads"},
+        "method_work": {"bytes_per_step": method_bytes(stats),
+                        "gb_per_s_over_count_pass": method_bytes(stats) / (count_pass_ms / 1e3) / 1e9,
+                        "count_pass_ms": count_pass_ms,
+                        "note": "the ray-by-ray method's algorithmic bytes (1 B per DDA step of every ray, 4 B per "
+                                "ancestor depth read, 4 B per rendered texel) over the count pass's time: the work "
+                                "rate the same results would need from a ray-by-ray walk (not a roofline: the "
+                                "owned-voxel kernels do not execute that walk)"},
+        "modes": modes,
+        "work_per_step": stats,
+        "kernel_ms_per_step": {k.replace("_ms", ""): v / steps for k, v in ktimes.items() if k.endswith("_ms")},
+        "sm_count": sm_count,
+        "clocks": clocks,
+    }
     m.close()
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
     return res
 
 
+def run_modes(mig, torch, m, prob, rays_per_step):
+    """The gain modes side by side (Table 2's absolute vs marginal columns, the paper's screen-space
+    interval overlap against voxel-centre samples, panoramic counting), each through the public
+    host-array call: median of 3 after one warm-up (a mode slower than 2 s: that first call alone)."""
+    s = prob.sensor
+    modes, yaws = {}, {}
+    for name, md in (("marginal_samples", mig.MODE_MARGINAL), ("marginal_intervals", mig.MODE_INTERVAL),
+                     ("single_parent", mig.MODE_SINGLE_PARENT), ("absolute", mig.MODE_ABSOLUTE),
+                     ("panoramic", mig.MODE_PANORAMIC)):
+        if md == mig.MODE_PANORAMIC and s.pitch_deg != 0:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+        first_ms = (time.perf_counter() - t0) * 1e3
+        ts = []
+        for _ in range(3 if first_ms < 2000 else 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = mig.tree_eval(m, prob.tree.parent, prob.tree.pos, s, mode=md)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = float(np.median(ts)) if ts else first_ms
+        modes[name] = {"ms_per_replan": ms, "rays_per_s": rays_per_step / (ms / 1e3),
+                       "marg_sum": int(g["marg"].sum()), "abs_sum": int(g["abs"].sum())}
+        if md == mig.MODE_PANORAMIC:
+            modes[name]["note"] = ("rays_per_s counts the pinhole rays the mode stands in for (nodes x K x W x H); "
+                                   "it casts nodes x A x H with A azimuth columns")
+        yaws[name] = g["yaw"]
+    for name in modes:  # how often each mode picks the same viewpoint as voxel-centre samples
+        modes[name]["same_yaw_as_samples"] = float(np.mean(yaws[name] == yaws["marginal_samples"]))
+    return modes
+
+
 # ----------------------------------------------------------------------------- batched (config 4)
-def run_batched(args):
-    """64 trees on 64 maps: one persistent launch per step (graph replay), against the same trees
-    evaluated by 64 sequential plain launches. value = batched rays/s; both arms end to end
-    through the host-array calls (plans up, results down inside the timed region)."""
+def golden_batched_check(probs, outs):
+    """True/False against the stored oracle results of the 64-tree workload when present and the
+    inputs match; None otherwise."""
+    import synth
+    path = os.path.join(ROOT, "tests", "golden", "batched_oracle.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    off = g["offsets"]
+    if len(off) - 1 != len(probs):
+        return None
+    for i, p in enumerate(probs):
+        if synth.sha256(p.map.grid, p.tree.parent, p.tree.pos) != str(g["inputs_sha256"][i]):
+            return None
+    return all(np.array_equal(o[k], g[k][off[i]:off[i + 1]]) for i, o in enumerate(outs) for k in ("abs", "marg", "yaw"))
+
+
+def batched_compare(repeats=3, small=False):
+    """64 trees on 64 maps: one batched call per step (graph replay) against the same trees evaluated
+    by 64 sequential plain calls; both end to end through the host-array calls (plans up, results
+    down inside the timed region), alternating, `repeats` times each."""
     import torch
 
     import paper_2609_40297_gb300 as mig
     import synth
 
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    small = args.workload == "batched_small"
+    init_dist(local)
     if small:
         probs = synth.batched_small(seed_base=606 + 1000 * rank)
-        n_trees = len(probs)
     else:
-        n_trees = int(os.environ.get("MIG_BATCH_TREES", "64"))
-        probs = synth.batched(seed_base=404 + 1000 * rank, n_trees=n_trees)
+        probs = synth.batched(seed_base=404 + 1000 * rank, n_trees=int(os.environ.get("MIG_BATCH_TREES", "64")))
+    n_trees = len(probs)
     stream = torch.cuda.Stream(local)
     ctx = mig.Context(local, stream=stream)
     dev_maps = {}  # one device map per distinct map (small trees share their map)
@@ -418,12 +450,10 @@ def run_batched(args):
     def plain_step():
         return [mig.tree_eval(m, *t) for m, t in zip(maps, trees)]
 
-    for _ in range(args.warmup):
-        ref = batched_step()
+    ref = batched_step()
     plain = plain_step()
     same = all(np.array_equal(a[k], b[k]) for a, b in zip(ref, plain) for k in ("abs", "marg", "yaw"))
-    if ws > 1:
-        torch.distributed.barrier()
+    golden = None if small else golden_batched_check(probs, ref)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
@@ -432,101 +462,80 @@ def run_batched(args):
     tw, th, cps, eng0 = ctx.get_tiles()
     for eng in (0, 1):
         ctx.set_tiles(tw, th, cps, eng)
-        for _ in range(2):
-            batched_step()
+        batched_step()
         t0 = time.perf_counter()
         batched_step()
         engine_ms[eng] = (time.perf_counter() - t0) * 1e3
     best_engine = min(engine_ms, key=engine_ms.get)
     ctx.set_tiles(tw, th, cps, best_engine)
     batched_step()
-    tb = []
-    for _ in range(args.steps):
+    tb, tp = [], []
+    for _ in range(repeats):
         t0 = time.perf_counter()
         batched_step()
         tb.append(time.perf_counter() - t0)
-    tp = []
-    for _ in range(max(1, args.steps // 2)):
         t0 = time.perf_counter()
         plain_step()
         tp.append(time.perf_counter() - t0)
     clocks = sampler.stop()
     caps, reps = ctx.graph_stats()
-    tbatch, tplain = max_over_ranks(float(np.sum(tb)), torch.device("cuda", local)), float(np.mean(tp))
-    value = ws * rays * len(tb) / tbatch
-    res = None
-    if rank == 0:
-        res = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": tbatch / len(tb) * 1e3, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 fixed point (u8 map)",
-               "data": "synthetic (seeded; stands in for the paper's Gazebo worlds)",
-               "config": {"workload": (f"batched small trees: {n_trees} trees, 16 per map on {len(dev_maps)} rooms maps "
-                                       "400x400x100 @0.1 m, trees U[20,60] nodes, depth U[2,5], 64x48 rays, K=16, 6 m "
-                                       "(short-horizon replans; not one of the paper's configurations)") if small else
-                                      (f"batched: {n_trees} trees on {n_trees} rooms maps 400x400x100 @0.1 m, "
-                                       "trees U[50,2000] nodes, depth U[3,15], ray grids 64x48..320x240, K=16, 6 m"),
-                          "nodes": nodes, "rays_per_step": rays,
-                          "l2": f"inputs ({len(dev_maps)} maps, {len(dev_maps) * 16} MB) larger than L2",
-                          "parallelism": f"replicas x{ws}"},
-               "replans_per_s": ws * n_trees * len(tb) / tbatch,
-               "plain": {"ms_per_step": tplain * 1e3, "rays_per_s": rays / tplain,
-                         "replans_per_s": n_trees / tplain, "launches": f"{n_trees} sequential mig_tree_eval calls"},
-               "batched_vs_plain_speedup": tplain / (tbatch / len(tb)),
-               "results_identical_to_plain": bool(same),
-               "graph": {"captures": caps, "replays": reps},
-               "engine_ms": {"persistent_dataflow": engine_ms[0], "stream_chains": engine_ms[1]},
-               "engine": ["persistent_dataflow", "stream_chains"][best_engine],
-               "e2e": {"value": value, "unit": "rays/s",
-                       "h2d_bytes_per_step": int(sum(p.tree.n * 16 for p in probs)),
-                       "d2h_bytes_per_step": int(nodes * 12)},
-               "gpu_launches": int(len(tb) * (sum(3 * (int(p.tree.depth().max()) + 1) - 1 for p in probs)
-                                             if best_engine == 1 else 1)),
-               "clocks": clocks}
-    for m in dev_maps.values():
-        m.close()
+    for mm in dev_maps.values():
+        mm.close()
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-    return res
+    tbm, tpm = float(np.median(tb)), float(np.median(tp))
+    desc = ((f"batched small trees: {n_trees} trees, 16 per map on {len(dev_maps)} rooms maps 400x400x100 @0.1 m, "
+             "trees U[20,60] nodes, depth U[2,5], 64x48 rays, K=16, 6 m (short-horizon replans; not one of the "
+             "paper's configurations)") if small else
+            (f"batched: {n_trees} trees on {n_trees} rooms maps 400x400x100 @0.1 m, trees U[50,2000] nodes, "
+             "depth U[3,15], ray grids 64x48..320x240, K=16, 6 m"))
+    return {
+        "workload": desc, "trees": n_trees, "nodes": nodes, "rays_per_step": rays,
+        "repeats": repeats,
+        "batched": {"ms": spread([x * 1e3 for x in tb]), "replans_per_s": n_trees / tbm, "rays_per_s": rays / tbm,
+                    "engine": ["persistent_dataflow", "stream_chains"][best_engine]},
+        "plain": {"ms": spread([x * 1e3 for x in tp]), "replans_per_s": n_trees / tpm, "rays_per_s": rays / tpm,
+                  "launches": f"{n_trees} sequential mig_tree_eval calls"},
+        "batched_vs_plain_speedup": tpm / tbm,
+        "speedup_range": [min(tp) / max(tb), max(tp) / min(tb)],
+        "results_identical_to_plain": bool(same),
+        "results_identical_to_oracle": golden,
+        "engine_ms": {"persistent_dataflow": engine_ms[0], "stream_chains": engine_ms[1]},
+        "graph": {"captures": caps, "replays": reps},
+        "e2e": {"h2d_bytes_per_step": int(sum(p.tree.n * 16 for p in probs)), "d2h_bytes_per_step": int(nodes * 12)},
+        "l2": f"inputs ({len(dev_maps)} maps, {len(dev_maps) * 16} MB) larger than L2",
+        "clocks": clocks,
+    }
 
 
 # ----------------------------------------------------------------------------- serving (config 5)
-def run_serving(args):
-    """16 robots on 4 rooms maps, Poisson arrivals (20 Hz each), a 10 % map update before each
-    request, trees of U[100,1500] nodes. Served arm: the continuous-batching server, arrivals
-    replayed in real time for a bounded window, latency = submit -> results on the host. Plain
-    arm: the same requests in arrival order through lone mig_tree_eval calls, as a FIFO
-    single-server queue on the measured service times."""
+def serving_compare(window_s, rate_hz, inflight=4):
+    """16 robots on 4 rooms maps, Poisson arrivals (rate_hz each) for window_s seconds, a 10 % map
+    update before each request, trees of U[100,1500] nodes. Served arm: the continuous-batching
+    server, arrivals replayed in real time, latency = arrival -> results on the host. Plain arm:
+    the same requests in arrival order through lone mig_tree_eval calls, as a FIFO single-server
+    queue on the measured service times."""
     import torch
 
     import paper_2609_40297_gb300 as mig
     import synth
 
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    window = float(os.environ.get("MIG_SERVE_SECONDS", "2.0"))
-    rate = float(args.serve_rate_hz)
-    maps_spec, pools, events, sensor = synth.serving_trace(seed=505 + 1000 * rank, duration_s=window, rate_hz=rate)
-    rng = np.random.default_rng(77 + rank)
-    updates = [synth.map_update_box(rng, maps_spec[mi], 0.10) for (_, _, mi, _) in events]
+    init_dist(local)
+    maps_spec, pools, events, sensor, updates = synth.serving_requests(seed=505 + 1000 * rank, duration_s=window_s,
+                                                                       rate_hz=rate_hz, update_seed=77 + rank)
     ctx = mig.Context(local, stream=torch.cuda.Stream(local))
 
     def fresh_maps():
-        return [mig.Map(ctx, m.grid, m.voxel_size, m.origin) for m in maps_spec]
+        return [mig.Map(ctx, mm.grid, mm.voxel_size, mm.origin) for mm in maps_spec]
 
-    # ---- warm-up (camera tables, kernels, allocator pools)
     wm = fresh_maps()
     t0_tree = pools[0][1][0]
-    for _ in range(args.warmup):
+    for _ in range(3):
         mig.tree_eval(wm[0], t0_tree.parent, t0_tree.pos, sensor)
-    for m in wm:
-        m.close()
+    for mm in wm:
+        mm.close()
     # ---- served arm: real-time replay
     maps = fresh_maps()
-    inflight = int(os.environ.get("MIG_SERVE_INFLIGHT", "4"))
     srv = mig.Server(ctx, arena_budget_bytes=8 << 30, max_inflight=inflight)
     tickets = [None] * len(events)
     start = time.perf_counter()
@@ -546,17 +555,19 @@ def run_serving(args):
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
-    lat = []
-    for t, _ in tickets:
+    lat, done_at = [], []
+    for i, (t, _) in enumerate(tickets):
         while not srv.poll(t, timeout_us=10_000_000):
             pass
-        lat.append(srv.timing(t)["done_us"] / 1e3)
+        tm = srv.timing(t)
+        lat.append(tm["done_us"] / 1e3)
+        done_at.append(events[i][0] + tm["done_us"] / 1e6)  # relative to the first arrival's clock
     t_end = time.perf_counter()
     clocks = sampler.stop()
     served_results = [out for _, out in tickets]
     srv.close()
-    for m in maps:
-        m.close()
+    for mm in maps:
+        mm.close()
     served_span = t_end - start
     # ---- plain arm: the same requests one by one (FIFO queue on measured service times)
     maps = fresh_maps()
@@ -573,35 +584,35 @@ def run_serving(args):
         finish = max(finish, t_arr) + sv
         lat_plain.append((finish - t_arr) * 1e3)
         same &= all(np.array_equal(out[k], served_results[i][k]) for k in ("abs", "marg", "yaw"))
-    for m in maps:
-        m.close()
+    for mm in maps:
+        mm.close()
     ctx.close()
     n = len(events)
     plain_span = finish
     rays = sum(pools[rid][1][ti].n for (_, rid, _, ti) in events) * sensor.yaw_bins * sensor.width * sensor.height
-    res = None
-    if rank == 0:
-        res = {"metric": METRIC, "value": ws * n / served_span, "unit": "replans/s", "n_gpus": ws,
-               "steps": n, "warmup": args.warmup, "ms_per_step": served_span / n * 1e3, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 fixed point (u8 map)",
-               "data": "synthetic (seeded Poisson trace; stands in for robots replanning online)",
-               "config": {"workload": f"serving: 16 robots on 4 rooms maps 400x400x100 @0.1 m, Poisson {rate:g} Hz each "
-                                      f"for {window:g} s of arrivals ({n} requests), trees U[100,1500] nodes, "
-                                      "160x120 rays, K=16, 10% map update before each request",
-                          "max_inflight": inflight, "parallelism": f"replicas x{ws}"},
-               "served": {"replans_per_s": n / served_span, "rays_per_s": rays / served_span,
-                          "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}},
-               "plain": {"replans_per_s": n / plain_span, "rays_per_s": rays / plain_span,
-                         "latency_ms": {"p50": float(np.percentile(lat_plain, 50)),
-                                        "p99": float(np.percentile(lat_plain, 99))},
-                         "mean_service_ms": float(np.mean(service)) * 1e3},
-               "served_vs_plain_replans": (n / served_span) / (n / plain_span),
-               "results_identical_alone_vs_mix": bool(same),
-               "e2e": {"value": ws * n / served_span, "unit": "replans/s",
-                       "h2d_bytes_per_step": int(np.mean([pools[r][1][t].n * 16 for (_, r, _, t) in events])),
-                       "d2h_bytes_per_step": int(np.mean([pools[r][1][t].n * 12 for (_, r, _, t) in events]))},
-               "gpu_launches": None, "clocks": clocks}
-    return res
+    backlog = int(sum(1 for d in done_at if d > window_s))
+    return {
+        "workload": (f"serving: 16 robots on 4 rooms maps 400x400x100 @0.1 m, Poisson {rate_hz:g} Hz each for "
+                     f"{window_s:g} s of arrivals ({n} requests), trees U[100,1500] nodes, 160x120 rays, K=16, "
+                     "10% map update before each request"),
+        "requests": n, "max_inflight": inflight,
+        "offered_replans_per_s": n / window_s,
+        "served": {"replans_per_s": n / served_span, "rays_per_s": rays / served_span, "span_s": served_span,
+                   "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}},
+        "plain": {"replans_per_s": n / plain_span, "rays_per_s": rays / plain_span, "span_s": plain_span,
+                  "latency_ms": {"p50": float(np.percentile(lat_plain, 50)),
+                                 "p99": float(np.percentile(lat_plain, 99))},
+                  "mean_service_ms": float(np.mean(service)) * 1e3},
+        "served_vs_plain_replans": plain_span / served_span,
+        "queue": {"backlog_at_window_end": backlog,
+                  "growth_per_s": max(0.0, n / window_s - n / served_span),
+                  "note": "requests not yet completed when the last arrival came, and the offered minus the served "
+                          "rate: positive when the offered load exceeds the GPU's capacity"},
+        "results_identical_alone_vs_mix": bool(same),
+        "e2e": {"h2d_bytes_per_step": int(np.mean([pools[r][1][t].n * 16 for (_, r, _, t) in events])),
+                "d2h_bytes_per_step": int(np.mean([pools[r][1][t].n * 12 for (_, r, _, t) in events]))},
+        "clocks": clocks,
+    }
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -639,10 +650,12 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=Fal
                           node_mask=mask, n_threads=n_threads)
     dt = time.perf_counter() - t0
     rays = m * s.yaw_bins * s.width * s.height
+    full_rays = prob.tree.n * s.yaw_bins * s.width * s.height
     out = {"value": rays / dt, "unit": "rays/s", "cores": n_threads or os.cpu_count(), "cpu": cpu_model(),
            "kind": "oracle",
            "sample": f"{m} of {prob.tree.n} nodes (all nodes of depth <= {sample_depth}), all {s.yaw_bins} yaws, "
-                     f"{s.width}x{s.height} rays; {dt:.1f} s", "seconds": dt}
+                     f"{s.width}x{s.height} rays; {dt:.1f} s",
+           "seconds": dt, "full_tree_seconds_extrapolated": full_rays / (rays / dt)}
     if with_gap:
         # gap of the depth-buffer marginal gain to the exact one (Eq. 2 with the same yaws, Sec. V-A),
         # both from the oracle on the same sample (the CUDA path is bit-identical to the oracle's DB part)
@@ -686,14 +699,31 @@ def cpu_baseline(workload, sample_depth=None, with_gap=False, with_mode_gaps=Fal
     return out
 
 
+def add_cpu_baseline(res, workload, with_modes):
+    cb = cpu_baseline(workload, with_gap=True, with_mode_gaps=with_modes)
+    res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample",
+                                              "full_tree_seconds_extrapolated")}
+    for key in ("gap_to_exact", "gap_to_exact_intervals", "gap_to_exact_panoramic", "exact_yaw"):
+        if cb.get(key):
+            res[key] = cb[key]
+    # the same oracle on one core, on a smaller sample (a few seconds)
+    c1 = cpu_baseline(workload, sample_depth={"tiny": 10, "paper_scale": 3, "large": 0}[workload], n_threads=1)
+    res["cpu_baseline_single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")}
+
+
+# ----------------------------------------------------------------------------- reference arm
+REFERENCE_SAMPLE_DEPTH = {"large": 1, "paper_scale": 3, "tiny": 10}
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return None
+    workload = args.workload if args.workload in REFERENCE_SAMPLE_DEPTH else "large"
     cb = None
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(args.workload)
+        r = cpu_baseline(workload, sample_depth=REFERENCE_SAMPLE_DEPTH[workload])
         if i >= args.warmup:
             vals.append(r["value"])
         cb = r
@@ -703,9 +733,16 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": cb["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64 fixed point (u8 map)", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC[args.workload], "sample": cb["sample"]},
+            "config": {"workload": WORKLOAD_DESC[workload], "sample": cb["sample"]},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- main
+def summary(r):
+    keys = ("value", "unit", "ms_per_step", "replans_per_s", "nodes_per_s", "replan_latency_ms", "e2e",
+            "results_match_host_path", "kernel_ms_per_step", "roofline", "method_work", "config")
+    return {k: r[k] for k in keys if k in r}
 
 
 def main():
@@ -714,38 +751,63 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper_scale",
-                    choices=["paper_scale", "tiny", "large", "batched", "batched_small", "serving"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "large", "paper_scale", "tiny", "batched", "batched_small", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison (interval, absolute)")
-    ap.add_argument("--serve-rate-hz", type=float, default=20.0,
-                    help="serving workload: Poisson request rate per robot (20 Hz offers ~9x the GPU's capacity)")
+    ap.add_argument("--no-extras", action="store_true", help="headline: skip the batched and serving parts")
+    ap.add_argument("--serve-rate-hz", type=float, default=20.0, help="serving: Poisson request rate per robot")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="serving: arrival window (the workload specifies 30 s; at 20 Hz per robot the queue grows
+                         "by ~280 requests per second, so the default run replays the first 3 s)")
+    ap.add_argument("--batch-repeats", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    ws, rank, _ = dist_env()
     if args.impl == "reference":
         res = run_reference(args)
         if res is not None:
             print(json.dumps(res))
         return
+    res = None
     if args.workload in ("batched", "batched_small"):
-        res = run_batched(args)
+        b = batched_compare(repeats=max(args.batch_repeats, args.steps), small=args.workload == "batched_small")
+        if rank == 0:
+            tb = b["batched"]["ms"]["median"] / 1e3
+            res = {"metric": METRIC, "value": ws * b["rays_per_step"] / tb, "unit": "rays/s", "n_gpus": ws,
+                   "steps": b["repeats"], "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True,
+                   "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": DATA,
+                   "config": {"workload": b["workload"], "parallelism": f"replicas x{ws}"},
+                   "e2e": {"value": ws * b["rays_per_step"] / tb, "unit": "rays/s", **b["e2e"]},
+                   "gpu_launches": None, "batched": b, "clocks": b["clocks"]}
     elif args.workload == "serving":
-        res = run_serving(args)
+        sv = serving_compare(args.serve_seconds, args.serve_rate_hz)
+        if rank == 0:
+            res = {"metric": METRIC, "value": ws * sv["served"]["replans_per_s"], "unit": "replans/s", "n_gpus": ws,
+                   "steps": sv["requests"], "warmup": args.warmup, "ms_per_step": 1e3 / sv["served"]["replans_per_s"],
+                   "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
+                   "data": "synthetic (seeded Poisson trace; stands in for robots replanning online)",
+                   "config": {"workload": sv["workload"], "parallelism": f"replicas x{ws}"},
+                   "e2e": {"value": ws * sv["served"]["replans_per_s"], "unit": "replans/s", **sv["e2e"]},
+                   "gpu_launches": None, "serving": sv, "clocks": sv["clocks"]}
     else:
-        res = run_ours(args)
-    ws, rank, _ = dist_env()
+        workload = "large" if args.workload == "headline" else args.workload
+        res = measure_single(workload, args.steps, args.warmup,
+                             with_modes=not args.no_modes and args.workload != "headline")
+        if args.workload == "headline" and ws == 1 and not args.no_extras:
+            res["paper_scale"] = summary(measure_single("paper_scale", args.steps, args.warmup))
+            res["batched"] = batched_compare(repeats=args.batch_repeats)
+            res["serving"] = {
+                "as_specified": serving_compare(args.serve_seconds, args.serve_rate_hz),
+                "feasible_load": serving_compare(10.0, 2.0),
+            }
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            add_cpu_baseline(res, workload, with_modes=not args.no_modes and args.workload != "headline")
+    if ws > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
     if rank == 0 and res is not None:
-        if ws == 1 and not args.no_cpu_baseline and args.workload in ("paper_scale", "tiny", "large"):
-            cb = cpu_baseline(args.workload, with_gap=True, with_mode_gaps=not args.no_modes)
-            res["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")}
-            res["gap_to_exact"] = cb.get("gap_to_exact")
-            for key in ("gap_to_exact_intervals", "gap_to_exact_panoramic", "exact_yaw"):
-                if cb.get(key):
-                    res[key] = cb[key]
-            # the same oracle on one core, on a smaller sample (a few seconds)
-            c1 = cpu_baseline(args.workload, sample_depth={"tiny": 10, "paper_scale": 3, "large": 0}[args.workload],
-                              n_threads=1)
-            res["cpu_baseline_single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "cpu", "kind", "sample")}
         print(json.dumps(res))
 
 

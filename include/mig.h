@@ -200,9 +200,11 @@ mig_status mig_tree_score_device(mig_ctx *ctx, int n, const int32_t *parent, con
  * MIG_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until the process exits.
  * A tree needs about n * width * height * 4 bytes plus n * (K * 8 + 64 + 4 * max_depth) bytes;
  * a larger request returns MIG_EINVAL with the size in mig_last_error. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. Every call shares the one array: calls whose work overlaps on
- * the GPU (other streams, other contexts on the same device) race and corrupt each other.
+ * device looks up the array's device address (cudaGetSymbolAddress) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not call
+ * cudaDeviceReset on that device afterwards (the array may move). Every call shares the one
+ * array: calls whose work overlaps on the GPU (other streams, other contexts on the same
+ * device) race and corrupt each other. It counts with the ray-by-ray kernel (identical results).
  * --------------------------------------------------------------------------------------- */
 #define MIG_NOALLOC_SCRATCH_BYTES (64u << 20)
 mig_status mig_tree_eval_device_noalloc(mig_map *map, int n, const int32_t *parent, const float *pos_m,
@@ -268,7 +270,8 @@ mig_status mig_batch_trace_read(mig_ctx *ctx, mig_trace_rec *out, int cap, int *
 
 /* ---------------------------------------------------------------------------------------
  * Serving: continuous batching of replanning requests. Submitted trees wait in an admission
- * queue until depth-buffer arena bytes (nodes * W * H * 4 plus counters) fit the budget, then
+ * queue until their device bytes (depth-buffer arena nodes * W * H * 4, counters, step counts) plus
+ * the bytes already held (requests in flight and map snapshots) fit the budget, then
  * join the device work of the requests already running; each request's results are the same
  * as a lone mig_tree_eval on the map contents at submission time. The descriptor's host arrays
  * are copied at submit; outputs are written when the request completes. A worker thread
@@ -284,6 +287,11 @@ mig_status mig_server_poll(mig_server *srv, uint64_t ticket, int64_t timeout_us)
  * before every request submitted after it (requests keep their map snapshot). */
 mig_status mig_server_map_update(mig_server *srv, mig_map *map, int x0, int y0, int z0, int dx, int dy, int dz,
                                  const uint8_t *host_voxels);
+/* Device bytes the server holds: requests in flight (plans, counters, step counts, depth-buffer
+ * arenas) and map snapshots (a map updated while requests still read it keeps its previous grid
+ * until they finish; those copies count against the budget as well, and an update whose copy would
+ * not fit waits for requests to finish); peak = the largest sum of the two so far. */
+mig_status mig_server_memory(mig_server *srv, uint64_t *in_use, uint64_t *snapshots, uint64_t *peak);
 /* Per-request timing (microseconds since submit): admitted, started on device, completed. */
 mig_status mig_server_timing(mig_server *srv, uint64_t ticket, double *admit_us, double *start_us, double *done_us);
 void mig_server_destroy(mig_server *srv);
@@ -307,14 +315,20 @@ typedef struct mig_kernel_times {
     uint64_t cast_launches, voxel_launches;
 } mig_kernel_times;
 /* Count kernels of the sample modes (marginal, single parent, absolute; no counterpart in the
- * paper, and both give identical results): ray_by_ray = 0 selects owned-voxel counting (the
- * default: each pixel ray is cast to its stopping point once, then every unknown voxel of the
- * frustum is tested against the ray of the pixel that owns it), 1 ray-by-ray counting (every ray
- * owner-tests every unknown voxel it crosses). The owned-voxel kernels keep one uint16 step count
- * per (node, yaw, pixel) of a level in a buffer of at most steps_budget_bytes (0 = the default,
- * 1 GiB); a level whose pairs do not fit is counted in chunks (at least one pair per chunk).
- * Errors: MIG_EINVAL (ctx NULL). */
-mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int ray_by_ray, uint64_t steps_budget_bytes);
+ * paper; all give identical results). Owned-voxel counting casts each pixel ray once to its first
+ * occupied voxel, then tests every unknown voxel of the frustum against the ray of the pixel that
+ * owns it (its centre's projection): MIG_COUNT_PAIRS enumerates each (node, yaw) frustum,
+ * MIG_COUNT_NODES each node's voxels once for all yaws (at most 64 yaws; its ancestor test runs
+ * once per voxel), MIG_COUNT_AUTO (the default) takes the per-node pass when a voxel lies in at least
+ * 6 yaws' frusta on average. MIG_COUNT_RAYS walks every ray through every voxel it crosses and
+ * owner-tests the unknown ones. The owned-voxel kernels keep one uint16 step count per (node, yaw,
+ * pixel) of a level in a buffer of at most steps_budget_bytes (0 = the default, 1 GiB); a level
+ * that does not fit is counted in chunks. Errors: MIG_EINVAL (ctx NULL, unknown kernel). */
+#define MIG_COUNT_AUTO 0
+#define MIG_COUNT_RAYS 1
+#define MIG_COUNT_PAIRS 2
+#define MIG_COUNT_NODES 3
+mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int kernel, uint64_t steps_budget_bytes);
 mig_status mig_ctx_profile(mig_ctx *ctx, int enable);
 mig_status mig_ctx_profile_read(mig_ctx *ctx, mig_kernel_times *out);
 

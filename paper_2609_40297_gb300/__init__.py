@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmig.so")
 
 MIG_OK, MIG_EINVAL, MIG_ENOMEM, MIG_ECUDA, MIG_ETIMEOUT, MIG_EBUSY, MIG_ENOTFOUND = range(7)
+COUNT_AUTO, COUNT_RAYS, COUNT_PAIRS, COUNT_NODES = 0, 1, 2, 3
 MODE_MARGINAL, MODE_SINGLE_PARENT, MODE_ABSOLUTE, MODE_INTERVAL, MODE_PANORAMIC = 0, 1, 2, 3, 4
 BUILD_CHECKED = 1  # mig_build_flags(): the bounds-checked build
 STATUS_NAMES = {0: "MIG_OK", 1: "MIG_EINVAL", 2: "MIG_ENOMEM", 3: "MIG_ECUDA", 4: "MIG_ETIMEOUT", 5: "MIG_EBUSY",
@@ -36,7 +37,7 @@ EXPORTS = [
     "mig_batch_graph_stats", "mig_batch_trace", "mig_batch_trace_read", "mig_autotune",
     "mig_server_create", "mig_server_submit", "mig_server_poll", "mig_server_map_update", "mig_server_timing",
     "mig_server_destroy", "mig_ctx_profile", "mig_ctx_profile_read", "mig_tree_eval_stats", "mig_last_error",
-    "mig_build_flags", "mig_probe_gather", "mig_ctx_set_count_kernel",
+    "mig_build_flags", "mig_probe_gather", "mig_ctx_set_count_kernel", "mig_server_memory",
 ]
 
 
@@ -160,6 +161,7 @@ def lib():
                 "mig_build_flags": (i, []),
                 "mig_probe_gather": (st, [p, C.c_uint64, i, p]),
                 "mig_ctx_set_count_kernel": (st, [p, i, C.c_uint64]),
+                "mig_server_memory": (st, [p, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name, None)
@@ -250,10 +252,10 @@ class Context:
         check(lib().mig_batch_get_tiles(self.h, C.byref(t)))
         return (t.tile_w, t.tile_h, t.ctas_per_sm, t.engine)
 
-    def set_count_kernel(self, ray_by_ray=False, steps_budget_bytes=0):
-        """mig_ctx_set_count_kernel: False = owned-voxel counting (default), True = ray by ray;
-        steps_budget_bytes bounds the owned-voxel step-count buffer (0 = the default)."""
-        check(lib().mig_ctx_set_count_kernel(self.h, 1 if ray_by_ray else 0, int(steps_budget_bytes)))
+    def set_count_kernel(self, kernel=0, steps_budget_bytes=0):
+        """mig_ctx_set_count_kernel: COUNT_AUTO (0, default), COUNT_RAYS (1, also True), COUNT_PAIRS (2) or
+        COUNT_NODES (3); steps_budget_bytes bounds the owned-voxel step-count buffer (0 = the default)."""
+        check(lib().mig_ctx_set_count_kernel(self.h, int(kernel), int(steps_budget_bytes)))
 
     def profile(self, enable=True):
         check(lib().mig_ctx_profile(self.h, 1 if enable else 0))
@@ -454,6 +456,12 @@ class Server:
         if st in (MIG_EBUSY, MIG_ETIMEOUT):
             return False
         check(st)
+
+    def memory(self):
+        """mig_server_memory: device bytes of requests in flight, of map snapshots, and the peak sum."""
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        check(lib().mig_server_memory(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"in_use": a.value, "snapshots": b.value, "peak": c.value}
 
     def timing(self, ticket):
         a, b, c = C.c_double(), C.c_double(), C.c_double()

@@ -138,6 +138,12 @@ mig_status ctx_pano(mig_ctx *ctx, const Camera *ccam) {
     return MIG_OK;
 }
 
+void set_band(LevelParams &p, const Camera *cam) {
+    p.band_tlo = cam->band_tlo;
+    p.band_thi = cam->band_thi;
+    p.az_half = cam->az_half;
+}
+
 void set_pano_params(LevelParams &p, const Camera *cam, int32_t *pcnt) {
     p.pano_A = cam->pano_A;
     p.pano_Wc = cam->pano_Wc;
@@ -157,7 +163,7 @@ void launch_level_count(const mig_ctx *ctx, const LevelParams &p, int Ld, int co
         launch_pano_count(p, std::max(1, std::min((pitems + 7) / 8, ctx->num_sms * ctx->pano_ctas)), s);
         launch_pano_window(p, std::max(1, std::min((Ld * p.K + 255) / 256, 1024)), s);
     } else if (p.steps) {
-        launch_vox_level(p, (long long)Ld * p.K, ctx->num_sms, ctx->vox_ctas, s);
+        launch_vox_level(p, (long long)Ld * p.K, ctx->num_sms, ctx->vox_ctas, ctx->node_ctas, s);
     } else {
         launch_count(p, std::max(1, std::min((items + 7) / 8, count_cap)), s);
     }
@@ -169,12 +175,16 @@ void launch_level_count_timed(mig_ctx *ctx, const LevelParams &p, int Ld, int co
         return;
     }
     const long long pairs = (long long)Ld * p.K;
-    for (long long q0 = 0; q0 < pairs; q0 += p.steps_cap) {
+    const int cap = vox_chunk_pairs(p);
+    for (long long q0 = 0; q0 < pairs; q0 += cap) {
         LevelParams c = p;
         c.q0 = (int)q0;
-        c.q1 = (int)std::min<long long>(pairs, q0 + p.steps_cap);
+        c.q1 = (int)std::min<long long>(pairs, q0 + cap);
         timed_launch(ctx, kProfCast, [&] { launch_cast_chunk(c, ctx->num_sms, ctx->stream); });
-        timed_launch(ctx, kProfVoxel, [&] { launch_voxel_chunk(c, ctx->num_sms, ctx->vox_ctas, ctx->stream); });
+        timed_launch(ctx, kProfVoxel, [&] {
+            if (node_pass(c)) launch_node_chunk(c, ctx->num_sms, ctx->node_ctas, ctx->stream);
+            else launch_voxel_chunk(c, ctx->num_sms, ctx->vox_ctas, ctx->stream);
+        });
     }
 }
 
@@ -259,6 +269,8 @@ static LevelParams level_params(const mig_map *m, const Camera *cam, const mig_c
     p.tile_h = ctx->tiles.tile_h;
     p.tiles_x = (p.W + p.tile_w - 1) / p.tile_w;
     p.tiles = p.tiles_x * ((p.H + p.tile_h - 1) / p.tile_h);
+    set_band(p, cam);
+    p.voxel_pass = ctx->voxel_pass;
     return p;
 }
 
@@ -298,6 +310,7 @@ mig_status mig_ctx_create(int device, void *stream, const mig_allocator *allocat
     ctx->interval_ctas = count_interval_ctas_per_sm();
     ctx->pano_ctas = pano_ctas_per_sm();
     ctx->vox_ctas = vox_ctas_per_sm();
+    ctx->node_ctas = node_ctas_per_sm();
     ctx->steps_budget = kStepsBudget;
     ctx->d_err = (int32_t *)ctx->alloc.alloc(256, ctx->stream);
     if (!ctx->d_err) return fail(MIG_ENOMEM, "ctx_create: allocation failed");
@@ -357,10 +370,12 @@ mig_status mig_ctx_sync(mig_ctx *ctx) {
     return MIG_OK;
 }
 
-mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int ray_by_ray, uint64_t steps_budget_bytes) {
+mig_status mig_ctx_set_count_kernel(mig_ctx *ctx, int kernel, uint64_t steps_budget_bytes) {
     if (!ctx) return fail(MIG_EINVAL, "ctx is NULL");
+    if (kernel < MIG_COUNT_AUTO || kernel > MIG_COUNT_NODES) return fail(MIG_EINVAL, "set_count_kernel: unknown kernel");
     std::lock_guard<std::mutex> lk(ctx->mu);
-    ctx->ray_count = ray_by_ray != 0;
+    ctx->ray_count = kernel == MIG_COUNT_RAYS;
+    ctx->voxel_pass = kernel == MIG_COUNT_RAYS ? MIG_COUNT_AUTO : kernel;
     ctx->steps_budget = steps_budget_bytes ? (size_t)steps_budget_bytes : kStepsBudget;
     return MIG_OK;
 }
@@ -568,7 +583,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     int Lmax = 1;
     for (int d = 0; d < L; ++d) Lmax = std::max(Lmax, plan.level_off[d + 1] - plan.level_off[d]);
     const int steps_cap = steps_cap_for(ctx, Lmax, K, cam->W, cam->H, mode);
-    const size_t o_steps = cv.take<uint16_t>(std::max<size_t>(1, (size_t)steps_cap * WH));
+    const size_t o_steps = cv.take<char>(steps_region_bytes(steps_cap, WH));
     // instrumented pass: the ray-by-ray count kernel is re-run into scratch counters afterwards,
     // for the method's own work counts (rays, DDA steps, owner tests) and as a cross-check
     const bool rerun = stats && steps_cap > 0;
@@ -615,6 +630,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
     MIG_CUDA_TRY(cudaMemsetAsync(p.bounds_err, 0, 4, ctx->stream));
 #endif
     p.steps = steps_cap ? (uint16_t *)(dev + o_steps) : nullptr;
+    p.vctr = steps_counter((uint16_t *)(dev + o_steps), steps_cap, WH);
     p.steps_cap = steps_cap;
     if (stats) {
         p.stats = (unsigned long long *)(dev + o_stats);
@@ -752,7 +768,7 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     // level sizes are known on the device only: the step-count buffer is sized for n nodes (its
     // chunks beyond a level's pairs return at once)
     const int steps_cap = steps_cap_for(ctx, n, K, cam->W, cam->H, MIG_MODE_MARGINAL);
-    const size_t o_steps = cv.take<uint16_t>(std::max<size_t>(1, (size_t)steps_cap * WH));
+    const size_t o_steps = cv.take<char>(steps_region_bytes(steps_cap, WH));
     char *dev = nullptr;
     st = ctx_workspace(ctx, cv.off, (void **)&dev);
     if (st != MIG_OK) return st;
@@ -805,6 +821,7 @@ mig_status mig_tree_eval_device(mig_map *m, int n, const int32_t *parent, const 
     p.mode = MIG_MODE_MARGINAL;
     p.max_anc = std::max(1, max_depth);
     p.steps = steps_cap ? (uint16_t *)(dev + o_steps) : nullptr;
+    p.vctr = steps_counter((uint16_t *)(dev + o_steps), steps_cap, WH);
     p.steps_cap = steps_cap;
     const int cap = ctx->num_sms * 16;
     const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));

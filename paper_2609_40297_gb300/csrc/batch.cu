@@ -21,6 +21,7 @@
 #include <memory>
 
 #include "batch.h"
+#include "voxcount.h"
 #include "dev_path.cuh"
 #include "kernels.h"
 
@@ -385,6 +386,7 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
         p.body = (const int4 *)it.cam->d_body;
         p.yawtab = it.cam->d_yaw;
+        set_band(p, it.cam);
         p.W = it.cam->W;
         p.H = it.cam->H;
         p.K = it.cam->K;
@@ -576,8 +578,8 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         int Lmax = 1;
         for (int d = 0; d <= pl.max_depth; ++d) Lmax = std::max(Lmax, pl.level_off[d + 1] - pl.level_off[d]);
         steps_cap[t] = steps_cap_for(ctx, Lmax, items[t].cam->K, items[t].cam->W, items[t].cam->H, items[t].mode);
-        stream_steps[oi % S] =
-            std::max(stream_steps[oi % S], (size_t)steps_cap[t] * items[t].cam->W * items[t].cam->H * sizeof(uint16_t));
+        stream_steps[oi % S] = std::max(stream_steps[oi % S],
+                                        steps_region_bytes(steps_cap[t], (size_t)items[t].cam->W * items[t].cam->H));
     }
     std::vector<size_t> o_steps(S);
     for (int i = 0; i < S; ++i) o_steps[i] = cv.take(std::max<size_t>(stream_steps[i], 1));
@@ -606,6 +608,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
         p.body = (const int4 *)it.cam->d_body;
         p.yawtab = it.cam->d_yaw;
+        set_band(p, it.cam);
         p.W = it.cam->W;
         p.H = it.cam->H;
         p.K = it.cam->K;
@@ -635,6 +638,9 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
     for (int oi = 0; oi < T; ++oi) {
         const int t = order[oi];
         lp[t].steps = steps_cap[t] ? (uint16_t *)(dev + o_steps[oi % S]) : nullptr;
+        lp[t].voxel_pass = ctx->voxel_pass;
+        lp[t].vctr = steps_counter((uint16_t *)(dev + o_steps[oi % S]), steps_cap[t],
+                                   (size_t)items[t].cam->W * items[t].cam->H);
         lp[t].steps_cap = steps_cap[t];
     }
     if (!ctx->batch) ctx->batch = new mig_ctx::Batch();

@@ -35,7 +35,7 @@ struct SegInfo {
 
 // Trees per persistent launch: their parameters travel in the kernel's parameter space (constant
 // bank, up to 32 KB), indexed by the warp-uniform tree number. Larger batches use several launches.
-constexpr int kBatchMaxTrees = 100;
+constexpr int kBatchMaxTrees = 96;
 
 struct BatchParams {
     const SegInfo *segs;        // by segment id

@@ -5,6 +5,7 @@
 // forward = world +x at yaw 0; pitch positive = nose down; yaw bin k at 2 pi k / K about +z.
 // Every value that decides a result is quantised here once (rays Q30, projection rows Q16);
 // all later steps run in integers on the device.
+#include <algorithm>
 #include <cmath>
 
 #include "mig_impl.h"
@@ -57,6 +58,42 @@ mig_status camera_build(const mig_sensor &s, Camera &c) {
             o[2] = q30(-(cy * cp + cz * sp));  // body up
             o[3] = q30(cz);                    // camera z of the unit ray
         }
+    }
+    // Elevation band and azimuth half-width of the frustum (culling bounds for the per-node voxel
+    // pass): without a vertical direction inside the frustum, both extremes lie on the image
+    // border, sampled densely here and widened by half a degree.
+    {
+        auto body_dir = [&](double a, double b, double out[3]) {
+            const double nrm = std::sqrt((a * a + b * b) + 1.0);
+            const double x = a / nrm, y = b / nrm, z = 1.0 / nrm;
+            out[0] = z * cp - y * sp;
+            out[1] = -x;
+            out[2] = -(y * cp + z * sp);
+        };
+        double elo = 1e9, ehi = -1e9, az = 0.0;
+        const int S = 4096;
+        for (int e = 0; e < 4; ++e) {
+            for (int t = 0; t <= S; ++t) {
+                const double f = (double)t / S * 2.0 - 1.0;
+                const double a = (e < 2 ? f : (e == 2 ? -1.0 : 1.0)) * t_h;
+                const double b = (e < 2 ? (e == 0 ? -1.0 : 1.0) : f) * t_v;
+                double d[3];
+                body_dir(a, b, d);
+                const double el = std::atan2(d[2], std::hypot(d[0], d[1]));
+                elo = std::min(elo, el);
+                ehi = std::max(ehi, el);
+                az = std::max(az, std::fabs(std::atan2(d[1], d[0])));
+            }
+        }
+        // the vertical directions in camera coordinates: up (0, -cp, -sp), down (0, cp, sp)
+        const bool up_in = -sp > 0.0 && std::fabs(cp / sp) <= t_v;
+        const bool down_in = sp > 0.0 && std::fabs(cp / sp) <= t_v;
+        const double margin = 0.5 * M_PI / 180.0;
+        elo -= margin;
+        ehi += margin;
+        c.band_thi = (up_in || ehi >= 89.5 * M_PI / 180.0) ? 1e30f : (float)std::tan(ehi);
+        c.band_tlo = (down_in || elo <= -89.5 * M_PI / 180.0) ? -1e30f : (float)std::tan(elo);
+        c.az_half = (up_in || down_in || az + margin >= M_PI) ? 3.2f : (float)(az + margin);
     }
     const double fx = ((double)W * 0.5) / t_h, fy = ((double)H * 0.5) / t_v;
     const double cxp = (double)W * 0.5, cyp = (double)H * 0.5;

@@ -260,6 +260,24 @@ __device__ __forceinline__ int floor_div_from(int64_t U, int64_t Z, float est, i
     return q;
 }
 
+// The pixel coordinate floor(U / Z) (Eq. 5) for Z > 0, and whether it lies in [0, bound): from a
+// float estimate of U / Z, moved by exact integer products until q Z <= U < (q + 1) Z. One product
+// and two comparisons when the estimate is right (the estimate only sets the start).
+__device__ __forceinline__ bool pixel_in(int64_t U, int64_t Z, float est, int bound, int &q) {
+    int c = __float2int_rd(fminf(fmaxf(est, -1.0f), (float)bound));
+    int64_t lo = (int64_t)c * Z;
+    while (lo > U) {
+        if (--c < 0) return false;
+        lo -= Z;
+    }
+    while (U - lo >= Z) {
+        if (++c >= bound) return false;
+        lo += Z;
+    }
+    q = c;
+    return c >= 0 && c < bound;
+}
+
 // Sec. IV-B: is the centre of voxel (x, y, z) observed by any ancestor (z <= stored depth)?
 // (The depth texel index is inside the buffer by construction: both pixel coordinates are clamped.)
 template <bool STATS, class HOT>
@@ -277,15 +295,13 @@ __device__ __forceinline__ bool observed(const HOT &p, const AncRec *anc, int na
         if constexpr (STATS) ++st_anc;
         if (Za <= 0) continue;
         const int64_t Ua = (int64_t)r0.z * ax + (int64_t)r0.w * ay + (int64_t)r1.x * az;
-        if (Ua < 0 || Ua >= (int64_t)p.W() * Za) continue;
         const int64_t Va = (int64_t)r1.y * ax + (int64_t)r1.z * ay + (int64_t)r1.w * az;
-        if (Va < 0 || Va >= (int64_t)p.H() * Za) continue;
         const float rx = xf - A.fx, ry = yf - A.fy, rz = zf - A.fz;
-        const float zi = __frcp_rn(fmaf(A.m[6], rx, fmaf(A.m[7], ry, A.m[8] * rz)));
+        const float zi = __fdividef(1.0f, fmaf(A.m[6], rx, fmaf(A.m[7], ry, A.m[8] * rz)));
         const float uf = fmaf(A.m[0], rx, fmaf(A.m[1], ry, A.m[2] * rz)) * zi;
         const float vf = fmaf(A.m[3], rx, fmaf(A.m[4], ry, A.m[5] * rz)) * zi;
-        const int pu = floor_div_from(Ua, Za, uf, p.W());
-        const int pv = floor_div_from(Va, Za, vf, p.H());
+        int pu, pv;
+        if (!pixel_in(Ua, Za, uf, p.W(), pu) || !pixel_in(Va, Za, vf, p.H(), pv)) continue;
         const uint32_t D = __ldg(A.D + pv * p.W() + pu);
         if constexpr (STATS) ++st_reads;
         if (Za < (((int64_t)D + 1) << 16)) return true;  // z <= D

@@ -52,8 +52,12 @@ struct LevelParams {
     // owned-voxel count (voxcount.cu): per-ray DDA step counts of a chunk of (node, yaw) pairs
     // [q0, q1) of the level, steps_cap pairs of W * H each; NULL = the ray-by-ray count kernel
     uint16_t *steps;
+    int32_t *vctr;  // work counter of the voxel pass (zeroed by the cast launch before it)
     int steps_cap;
     int q0, q1;
+    // per-node voxel pass: the frustum's elevation band (tangents) and azimuth half-width
+    float band_tlo, band_thi, az_half;
+    int voxel_pass;  // MIG_COUNT_AUTO, MIG_COUNT_PAIRS or MIG_COUNT_NODES
 };
 
 void launch_count(const LevelParams &p, int grid, cudaStream_t s);

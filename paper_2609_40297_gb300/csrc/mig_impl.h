@@ -57,6 +57,11 @@ struct Camera {
     std::vector<int32_t> yaw;   // K*kYawRec
     int32_t *d_body = nullptr;
     int32_t *d_yaw = nullptr;
+    // the frustum's extent about its yaw axis, for enumerating voxels once per node over all yaws
+    // (conservative culling bounds, not result-deciding): tangents of the lowest and highest
+    // elevation of a voxel centre that can project into the image, and the largest azimuth offset
+    // from the yaw direction (pi when the frustum holds the vertical)
+    float band_tlo = -1e30f, band_thi = 1e30f, az_half = 3.2f;
     // panoramic mode (built on first use; level camera only): A azimuth wedges of a yaw step's
     // `pano_step` columns each, Wc columns per yaw window
     int pano_A = 0, pano_Wc = 0, pano_step = 0;
@@ -111,7 +116,9 @@ struct mig_ctx {
     int interval_ctas = 1;     // resident interval-mode count CTAs per SM
     int pano_ctas = 1;         // resident panoramic count CTAs per SM
     int vox_ctas = 1;          // resident owned-voxel count CTAs per SM
+    int node_ctas = 1;         // resident per-node voxel-pass CTAs per SM
     bool ray_count = false;    // count with the ray-by-ray kernel instead of the owned-voxel kernels
+    int voxel_pass = MIG_COUNT_AUTO;  // owned-voxel pass: per (node, yaw) pair, per node, or chosen
     size_t steps_budget = 0;   // owned-voxel step-count buffer per evaluation (bytes; set at creation)
     std::vector<std::unique_ptr<mig::Camera>> cameras;
     mig::DevBuf ws;          // per-call workspace (plan, counters, outputs, arena)
@@ -146,6 +153,8 @@ mig_status ctx_pinned(mig_ctx *ctx, size_t bytes, void **out);
 mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out);
 // The panoramic tables of a context camera, built and uploaded on first use (ctx->mu held).
 mig_status ctx_pano(mig_ctx *ctx, const Camera *cam);
+// The frustum band of the per-node voxel pass, from the camera.
+void set_band(LevelParams &p, const Camera *cam);
 // Panoramic level parameters from the camera's tables; pcnt = n * A * 2 int32 of workspace.
 void set_pano_params(LevelParams &p, const Camera *cam, int32_t *pcnt);
 // One level's count pass for p.mode: the sample, interval or panoramic kernels (Ld = nodes of

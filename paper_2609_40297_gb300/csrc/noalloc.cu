@@ -41,6 +41,16 @@ __global__ void noalloc_camera_kernel(int4 *body, int W, int H, double t_h, doub
     }
 }
 
+// Copies part of the per-yaw table into the scratch. The values travel in the kernel's parameters
+// (captured by value at launch), so no host buffer has to outlive the call.
+constexpr int kYawChunk = 1024;  // int32 per launch (4 KiB of parameters)
+struct YawChunk {
+    int32_t v[kYawChunk];
+};
+__global__ void noalloc_yaw_kernel(int32_t *dst, int count, const YawChunk chunk) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = chunk.v[i];
+}
+
 std::mutex g_setup_mu;
 void *g_scratch_ptr[64] = {nullptr};
 
@@ -104,7 +114,8 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
         return fail(MIG_EINVAL, "tree_eval_device_noalloc: needs " + std::to_string(cv.off) + " bytes of scratch, above the " +
                                     std::to_string((size_t)MIG_NOALLOC_SCRATCH_BYTES) +
                                     "-byte maximum (about nodes * width * height * 4 bytes of depth buffers)");
-    // per-yaw rotation and projection rows from the host's libm, on the stack (no allocation)
+    // per-yaw rotation and projection rows from the host's libm, on the stack (no allocation); they
+    // reach the device as kernel parameters
     const double t_h = std::tan(((double)sensor->hfov_deg * 0.5) * (M_PI / 180.0));
     const double t_v = std::tan(((double)sensor->vfov_deg * 0.5) * (M_PI / 180.0));
     const double th = (double)sensor->pitch_deg * (M_PI / 180.0);
@@ -143,8 +154,12 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     cudaStream_t s = ctx->stream;
     // the scratch keeps the previous call's contents: clear what must start at zero
     MIG_CUDA_TRY(cudaMemsetAsync(dev, 0, zero_bytes, s));
-    // pageable source: the copy returns once the stack table has been staged
-    MIG_CUDA_TRY(cudaMemcpyAsync(dev + o_yaw, yaw_tab, (size_t)K * kYawRec * 4, cudaMemcpyHostToDevice, s));
+    for (int i0 = 0; i0 < K * kYawRec; i0 += kYawChunk) {
+        YawChunk c;
+        const int cnt = std::min(kYawChunk, K * kYawRec - i0);
+        std::memcpy(c.v, yaw_tab + i0, (size_t)cnt * 4);
+        noalloc_yaw_kernel<<<1, 256, 0, s>>>((int32_t *)(dev + o_yaw) + i0, cnt, c);
+    }
     noalloc_camera_kernel<<<(int)std::min<size_t>((WH + 255) / 256, 1024), 256, 0, s>>>((int4 *)(dev + o_body), W, H,
                                                                                       t_h, t_v, cp, sp);
     DevPlanParams dp{};
@@ -207,12 +222,13 @@ extern "C" mig_status mig_tree_eval_device_noalloc(mig_map *m, int n, const int3
     p.stats = nullptr;
     p.max_anc = std::max(1, max_depth);
     const int cap = ctx->num_sms * 16;
+    const int count_cap = ctx->num_sms * std::min(ctx->count_ctas, std::max(1, (int)ctx->tiles.ctas_per_sm));
     const int sel_grid = std::max(1, std::min((n + 127) / 128, 1024));
     for (int d = 0; d < L; ++d) {
         p.lvl = d;
-        launch_count(p, ctx->num_sms * ctx->count_ctas, s);
-        launch_select(p, sel_grid, s);
-        launch_render(p, cap, s);
+        timed_launch(ctx, kProfCount, [&] { launch_count(p, count_cap, s); });
+        timed_launch(ctx, kProfSelect, [&] { launch_select(p, sel_grid, s); });
+        timed_launch(ctx, kProfRender, [&] { launch_render(p, cap, s); });
     }
     MIG_CUDA_TRY(cudaGetLastError());
     return MIG_OK;

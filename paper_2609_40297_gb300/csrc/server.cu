@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -25,6 +26,7 @@
 #include <unordered_map>
 
 #include "kernels.h"
+#include "voxcount.h"
 #include "mig_impl.h"
 
 using namespace mig;
@@ -85,6 +87,9 @@ struct Carve {
 struct mig_server {
     mig_ctx *ctx = nullptr;
     size_t budget = 0, in_use = 0;
+    // device bytes of superseded map grids that requests in flight still read (copy-on-write
+    // snapshots), and the largest in_use + snapshot bytes seen; written by the worker only
+    std::atomic<size_t> snap_bytes{0}, peak_bytes{0};
     int max_inflight = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -121,7 +126,7 @@ size_t request_bytes(const Request &r) {
     cv.take(12 * n);
     cv.take(4 * n);
     cv.take(4 * std::max(1, pl.n_internal) * WH);
-    cv.take(std::max<size_t>(1, (size_t)r.steps_cap * WH * sizeof(uint16_t)));
+    cv.take(steps_region_bytes(r.steps_cap, WH));
     return cv.off;
 }
 
@@ -156,7 +161,7 @@ mig_status admit(mig_server *s, Request &r) {
     const size_t o_out = cv.take(12 * (size_t)n), o_sel = cv.take(4 * (size_t)n);
     const size_t o_arena = cv.take(4 * (size_t)std::max(1, pl.n_internal) * WH);
     const size_t o_pcnt = pano ? cv.take(8 * (size_t)n * r.cam->pano_A) : 0;
-    const size_t o_steps = cv.take(std::max<size_t>(1, (size_t)r.steps_cap * WH * sizeof(uint16_t)));
+    const size_t o_steps = cv.take(steps_region_bytes(r.steps_cap, WH));
     r.dev_bytes = cv.off;
     r.dev = (char *)ctx->alloc.alloc(r.dev_bytes, ctx->stream);
     if (!r.dev) return fail(MIG_ENOMEM, "server: request allocation failed");
@@ -191,6 +196,7 @@ mig_status admit(mig_server *s, Request &r) {
     p.grid = GridView{r.grid->ptr, m->nx, m->ny, m->nz, m->nbx, m->nby};
     p.body = (const int4 *)r.cam->d_body;
     p.yawtab = r.cam->d_yaw;
+    set_band(p, r.cam);
     p.W = r.cam->W;
     p.H = r.cam->H;
     p.K = r.cam->K;
@@ -217,9 +223,16 @@ mig_status admit(mig_server *s, Request &r) {
     p.max_anc = std::max(1, pl.max_depth);
     if (pano) set_pano_params(p, r.cam, (int32_t *)(r.dev + o_pcnt));
     p.steps = r.steps_cap ? (uint16_t *)(r.dev + o_steps) : nullptr;
+    p.vctr = steps_counter((uint16_t *)(r.dev + o_steps), r.steps_cap, WH);
+    p.voxel_pass = ctx->voxel_pass;
     p.steps_cap = r.steps_cap;
     r.level = 0;
     return MIG_OK;
+}
+
+void note_peak(mig_server *s) {
+    const size_t now = s->in_use + s->snap_bytes.load();
+    if (now > s->peak_bytes.load()) s->peak_bytes.store(now);
 }
 
 void release_grid(mig_server *s, Request &r) {
@@ -228,8 +241,15 @@ void release_grid(mig_server *s, Request &r) {
     if (r.grid->retired && r.grid->users == 0) {
         s->ctx->alloc.free(r.grid->ptr, r.grid->bytes, s->ctx->stream);
         r.grid->ptr = nullptr;
+        s->snap_bytes -= r.grid->bytes;
     }
     r.grid.reset();
+}
+
+// Would applying an update to map m now copy its grid (requests in flight still read it)?
+bool update_needs_copy(mig_server *s, mig_map *m) {
+    auto it = s->grids.find(m);
+    return it != s->grids.end() && it->second->ptr == m->d_grid && it->second->users > 0;
 }
 
 // Applies a map update (worker thread, ctx->mu held): copy-on-write if requests read the grid.
@@ -242,6 +262,7 @@ mig_status apply_update(mig_server *s, Update &u) {
         if (!fresh) return fail(MIG_ENOMEM, "server: map copy allocation failed");
         MIG_CUDA_TRY(cudaMemcpyAsync(fresh, m->d_grid, m->grid_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         g->retired = true;  // freed by the last request that reads it
+        s->snap_bytes += g->bytes;
         m->d_grid = fresh;
         current_grid(s, m);
     }
@@ -298,6 +319,11 @@ void worker_main(mig_server *s) {
         while (!s->queue.empty()) {
             Entry &e = s->queue.front();
             if (e.upd) {
+                // a copy-on-write snapshot counts against the budget too: while it would not fit,
+                // the update (and every entry behind it) waits for requests in flight to finish
+                if (!s->inflight.empty() && update_needs_copy(s, e.upd->map) &&
+                    s->in_use + s->snap_bytes.load() + e.upd->map->grid_bytes > s->budget)
+                    break;
                 lk.unlock();
                 mig_status st;
                 {
@@ -306,13 +332,16 @@ void worker_main(mig_server *s) {
                 }
                 lk.lock();
                 if (st != MIG_OK) s->fatal = mig_last_error();
+                note_peak(s);
                 s->queue.pop_front();
                 continue;
             }
             Request &r = *e.req;
             const size_t need = request_bytes(r);
             if ((int)s->inflight.size() >= s->max_inflight) break;
-            if (!s->inflight.empty() && s->in_use + need > s->budget) break;  // a lone request always runs
+            // map snapshots held for requests in flight count against the budget; a lone request
+            // always runs
+            if (!s->inflight.empty() && s->in_use + s->snap_bytes.load() + need > s->budget) break;
             std::unique_ptr<Request> rq = std::move(e.req);
             s->queue.pop_front();
             lk.unlock();
@@ -332,6 +361,7 @@ void worker_main(mig_server *s) {
                 continue;
             }
             s->in_use += rq->dev_bytes;
+            note_peak(s);
             s->inflight.push_back(std::move(rq));
         }
         if (s->inflight.empty()) {
@@ -509,6 +539,15 @@ extern "C" mig_status mig_server_timing(mig_server *s, uint64_t ticket, double *
     if (admit_us) *admit_us = us(r.t_admit);
     if (start_us) *start_us = us(r.t_start);
     if (done_us) *done_us = us(r.t_done);
+    return MIG_OK;
+}
+
+extern "C" mig_status mig_server_memory(mig_server *s, uint64_t *in_use, uint64_t *snapshots, uint64_t *peak) {
+    if (!s) return fail(MIG_EINVAL, "server_memory: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (in_use) *in_use = s->in_use;
+    if (snapshots) *snapshots = s->snap_bytes.load();
+    if (peak) *peak = s->peak_bytes.load();
     return MIG_OK;
 }
 

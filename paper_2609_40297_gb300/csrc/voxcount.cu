@@ -1,12 +1,14 @@
 // Owned-voxel count of one tree level (Sec. IV-B, the counts of Eq. 1 and Eq. 2 by depth
 // buffers), in two kernels per chunk of (node, yaw) pairs:
-//   cast_kernel  - every pixel ray of every pair runs the DDA to its stopping point and stores
-//                  the number of steps it takes (uint16 per ray);
+//   cast_kernel  - every pixel ray of every pair runs the DDA to its first occupied voxel within
+//                  range and stores that voxel's step index (uint16 per ray; kNoHit if none);
 //   voxel_kernel - for every pair, the voxels within range of the node are enumerated slice by
 //                  slice (z), rows clipped to the camera frustum; each unknown voxel goes to the
 //                  pixel that owns it (its centre's projection) and counts as absolute gain iff
-//                  that pixel's DDA visits it within the stored step count; counted voxels are
-//                  tested 32 at a time against the ancestors' depth buffers (marginal gain).
+//                  that pixel's DDA reaches it before the range and before its first occupied
+//                  voxel; counted voxels are tested against the ancestors' depth buffers
+//                  (marginal gain). Each test stage runs on full warps: the voxels that pass one
+//                  stage wait in a per-warp queue until 32 of them are ready for the next.
 // Results are identical to the ray-by-ray count kernel (and the CPU oracle) bit for bit.
 #include <cuda_runtime.h>
 
@@ -26,7 +28,6 @@ using namespace dev;
 
 constexpr int kCastWarps = 8;   // 256-thread CTAs, one ray per thread
 constexpr int kVoxWarps = 8;
-constexpr int kVoxQueue = 64;   // per-warp queue of counted samples waiting for the ancestor test
 
 __device__ __forceinline__ int level_pairs(const LevelParams &p) {
     return (p.level_off[p.lvl + 1] - p.level_off[p.lvl]) * p.K;
@@ -34,13 +35,16 @@ __device__ __forceinline__ int level_pairs(const LevelParams &p) {
 
 // ------------------------------------------------------------------------------ cast kernel
 // Warp work item = (pair q of the chunk, 8x4 pixel tile); one ray per lane.
+constexpr int kCastTileW = 8, kCastTileH = 4;
+
 template <bool STATS>
 __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams p) {
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.vctr = 0;  // the voxel pass that follows hands out work from 0
     const int l0 = p.level_off[p.lvl];
     const int q1 = min(p.q1, level_pairs(p));
     if (p.q0 >= q1) return;
-    const int tx = (p.W + 7) >> 3, ty = (p.H + 3) >> 2;
+    const int tx = (p.W + kCastTileW - 1) / kCastTileW, ty = (p.H + kCastTileH - 1) / kCastTileH;
     const long long items = (long long)(q1 - p.q0) * tx * ty;
     const size_t WH = (size_t)p.W * p.H;
     const uint8_t *bocc = p.grid.g + bocc_offset(p.grid.nx, p.grid.ny, p.grid.nz);
@@ -50,7 +54,7 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
         const int tile = (int)(it % (tx * ty));
         const int ql = (int)(it / (tx * ty));
         const int q = p.q0 + ql;
-        const int i = (tile % tx) * 8 + (lane & 7), j = (tile / tx) * 4 + (lane >> 3);
+        const int i = (tile % tx) * kCastTileW + (lane % kCastTileW), j = (tile / tx) * kCastTileH + lane / kCastTileW;
         if (i >= p.W || j >= p.H) continue;
         const int n = p.level_nodes[l0 + q / p.K];
         const int k = q % p.K;
@@ -59,8 +63,8 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
         const int32_t *yk = p.yawtab + k * 12;
         int dx, dy, dz;
         ray_dir(b, yk[0], yk[1], dx, dy, dz);
-        const uint32_t m = cast_steps<STATS>(p.grid.g, bocc, p.grid.nx, p.grid.ny, p.grid.nz, nd.x, nd.y, nd.z, dx, dy,
-                                             dz, p.Tq, st_fine, st_skip);
+        const uint32_t m = cast_hit<STATS>(p.grid.g, bocc, p.grid.nx, p.grid.ny, p.grid.nz, nd.x, nd.y, nd.z, dx, dy,
+                                           dz, p.Tq, st_fine, st_skip);
         p.steps[(size_t)ql * WH + (size_t)j * p.W + i] = (uint16_t)m;
         if constexpr (STATS) ++st_rays;
     }
@@ -77,30 +81,64 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
 }
 
 // ----------------------------------------------------------------------------- voxel kernel
+// Per-warp queues between the test stages: unknown voxels of the slice (x | y << 12), voxels whose
+// owner pixel's ray may reach them (x | y << 12 | pixel << 24), counted samples (x | y << 16 |
+// z << 32). Each holds fewer than 64 entries: a stage runs whenever 32 are waiting.
+struct VoxQueues {
+    unsigned long long unk[64], own[64], smp[64];
+};
+
+// Appends the lanes' `take` entries `val` to queue q holding n entries (in lane order).
+__device__ __forceinline__ void q_push(unsigned long long *q, int &n, bool take, unsigned long long val,
+                                       unsigned lt_mask) {
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (take) q[n + __popc(bal & lt_mask)] = val;
+    n += __popc(bal);
+    __syncwarp();
+}
+// Takes the first 32 entries of q (lane l gets entry l) and moves the rest to the front.
+__device__ __forceinline__ unsigned long long q_pop32(unsigned long long *q, int &n, int lane) {
+    const unsigned long long v = q[lane];
+    const unsigned long long rest = lane + 32 < n ? q[lane + 32] : 0ull;
+    __syncwarp();
+    if (lane + 32 < n) q[lane] = rest;
+    __syncwarp();
+    n -= 32;
+    return v;
+}
+
 // Warp work item = (pair q of the chunk, slice z of the node's range ball). Lanes take 32 rows
-// (y) of the slice at a time, clip each row to the frustum and the ball, and then walk the rows'
+// (y) of the slice at a time, clip each row to the frustum and the ball, and then load the rows'
 // voxels 32 at a time (flattened over the rows with a warp prefix sum).
 template <bool STATS>
-__global__ void __launch_bounds__(kVoxWarps * 32, 4) voxel_kernel(const LevelParams p) {
+__global__ void __launch_bounds__(kVoxWarps * 32, 3) voxel_kernel(const LevelParams p) {
     extern __shared__ AncRec s_anc_dyn[];
-    __shared__ unsigned long long s_q[kVoxWarps][kVoxQueue];
+    __shared__ VoxQueues s_vq[kVoxWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     AncRec *anc = s_anc_dyn + warp * p.max_anc;
-    unsigned long long *q = s_q[warp];
+    VoxQueues &Q = s_vq[warp];
     const int l0 = p.level_off[p.lvl];
     const int q1 = min(p.q1, level_pairs(p));
     if (p.q0 >= q1) return;
     const int Rv = (int)(p.Tq >> 16) + 2;    // voxels: every visited voxel's centre is nearer than T + 1
     const int slices = 2 * Rv + 1;
-    const long long items = (long long)(q1 - p.q0) * slices;
+    const int npairs = q1 - p.q0;
+    const int items = npairs * slices;
     const float R = (float)p.Tq * (1.0f / 65536.0f) + 1.0f, R2 = R * R;
     const int gnx = p.grid.nx, gny = p.grid.ny, gnz = p.grid.nz;
     const size_t WH = (size_t)p.W * p.H;
     uint32_t st_cand = 0, st_unk = 0, st_visit = 0, st_anc = 0, st_reads = 0;
     int cur_node = -1, na = 0;
-    for (long long it = (long long)blockIdx.x * kVoxWarps + warp; it < items; it += (long long)gridDim.x * kVoxWarps) {
-        const int ql = (int)(it / slices), zi = (int)(it % slices);
+    // items are handed out one at a time from the launch's counter: every pair's slice at the node's
+    // own height first, then outwards alternately above and below
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(p.vctr, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int rank = it / npairs, ql = it % npairs;
+        const int zi = Rv + ((rank & 1) ? (rank + 1) >> 1 : -(rank >> 1));
         const int qq = p.q0 + ql;
         const int n = p.level_nodes[l0 + qq / p.K], k = qq % p.K;
         const int4 nd = p.node[n];
@@ -125,14 +163,75 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 4) voxel_kernel(const LevelPar
         const int mz0 = yk[8], mz1 = yk[9], mz2 = yk[10];
         const float s16 = 1.0f / 65536.0f;
         const float Pxf = (float)nd.x * s16 - 0.5f, Pyf = (float)nd.y * s16 - 0.5f;
-        // the frustum of the owner rule as half-spaces of the centre offset: Z > 0, U >= 0,
-        // W Z - U > 0, V >= 0, H Z - V > 0 (Eq. 5; W Z - U and H Z - V in exact integers)
         HalfSpace hs[5];
         frustum_half_spaces(mu0, mu1, mu2, mv0, mv1, mv2, mz0, mz1, mz2, p.W, p.H, hs);
-        const HalfSpace &hz = hs[0], &hu = hs[1], &hv = hs[3];
+        const uint16_t *steps = p.steps + (size_t)ql * WH;
+        const int v0x = nd.x >> 16, v0y = nd.y >> 16, v0z = nd.z >> 16;
+        const int zq = (z << 16) + 32768 - nd.z;
+        int c_abs = 0, c_mrg = 0, nu = 0, no = 0, ns = 0;
+
+        // stage 2: owner pixel of 32 unknown voxel centres (Eq. 5), and the cheap reach test: a voxel
+        // is the (|x - x0| + |y - y0| + |z - z0|)-th of any ray that visits it, so it is reached only
+        // if that index is below the owner ray's first occupied voxel
+        auto owner_stage = [&](bool full) {
+            const bool have = full || lane < nu;
+            const unsigned long long e = full ? q_pop32(Q.unk, nu, lane) : Q.unk[lane];
+            bool keep = false;
+            int pix = 0;
+            if (have) {
+                const int x = (int)(e & 0xFFF), y = (int)((e >> 12) & 0xFFF);
+                const int rx = (x << 16) + 32768 - nd.x, ry = (y << 16) + 32768 - nd.y;
+                const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ry + (int64_t)mz2 * zq;
+                const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ry + (int64_t)mu2 * zq;
+                const int64_t V = (int64_t)mv0 * rx + (int64_t)mv1 * ry + (int64_t)mv2 * zq;
+                if (Z > 0) {
+                    const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(y) - Pyf;
+                    const float zi_ = __fdividef(1.0f, fmaf(hs[0].a, fxr, fmaf(hs[0].b, fyr, hs[0].c * rz)));
+                    const float uf = fmaf(hs[1].a, fxr, fmaf(hs[1].b, fyr, hs[1].c * rz)) * zi_;
+                    const float vf = fmaf(hs[3].a, fxr, fmaf(hs[3].b, fyr, hs[3].c * rz)) * zi_;
+                    int pu, pv;
+                    if (pixel_in(U, Z, uf, p.W, pu) && pixel_in(V, Z, vf, p.H, pv)) {
+                        pix = pv * p.W + pu;
+                        const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
+                        keep = man < (int)__ldg(steps + pix);
+                    }
+                }
+            }
+            if (!full) nu = 0;
+            q_push(Q.own, no, keep, (e & 0xFFFFFFull) | ((unsigned long long)pix << 24), lt_mask);
+        };
+        // stage 3: the exact visit test by the owner ray (event order of its DDA, range)
+        auto visit_stage = [&](bool full) {
+            const bool have = full || lane < no;
+            const unsigned long long e = full ? q_pop32(Q.own, no, lane) : Q.own[lane];
+            bool counted = false;
+            int x = 0, y = 0;
+            if (have) {
+                if constexpr (STATS) ++st_visit;
+                x = (int)(e & 0xFFF);
+                y = (int)((e >> 12) & 0xFFF);
+                const int pix = (int)(e >> 24);
+                int dx, dy, dz;
+                ray_dir(p.body[pix], ck, sk, dx, dy, dz);
+                counted = visit_index(nd.x, nd.y, nd.z, dx, dy, dz, x, y, z, p.Tq) >= 0;
+            }
+            if (!full) no = 0;
+            c_abs += counted;
+            q_push(Q.smp, ns, counted,
+                   (unsigned long long)x | ((unsigned long long)y << 16) | ((unsigned long long)z << 32), lt_mask);
+        };
+        // stage 4: the ancestor test of 32 counted samples (Sec. IV-B)
+        auto ancestor_stage = [&](bool full) {
+            const bool have = full || lane < ns;
+            const unsigned long long sm = full ? q_pop32(Q.smp, ns, lane) : Q.smp[lane];
+            if (have)
+                c_mrg += !observed<STATS>(HotDirect{p}, anc, na, (int)(sm & 0xFFFF), (int)((sm >> 16) & 0xFFFF),
+                                          (int)(sm >> 32), st_anc, st_reads);
+            if (!full) ns = 0;
+        };
+
         const float hy = sqrtf(h2);
         const int ylo = max(0, (int)floorf(Pyf - hy) - 1), yhi = min(gny - 1, (int)ceilf(Pyf + hy) + 1);
-        int c_abs = 0, c_mrg = 0, qn = 0;
         for (int yb = ylo; yb <= yhi; yb += 32) {
             // this lane's row: x range of the centres inside the ball and the frustum
             const int y = yb + lane;
@@ -157,66 +256,34 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 4) voxel_kernel(const LevelPar
                 r = min(r, 31);
                 const int rxa = __shfl_sync(0xffffffffu, xa, r);
                 const int rstart = __shfl_sync(0xffffffffu, incl - len, r);
-                bool counted = false;
-                int x = 0, yy = 0;
+                bool unk = false;
+                int x = 0;
                 if (f < tot) {
                     x = rxa + (f - rstart);
-                    yy = yb + r;
                     if constexpr (STATS) ++st_cand;
-                    const uint32_t addr = ((uint32_t)z * (uint32_t)gny + (uint32_t)yy) * (uint32_t)gnx + (uint32_t)x;
-                    if (load_code(p.grid.g, addr, p.grid, p.bounds_err) == kUnknown) {
-                        if constexpr (STATS) ++st_unk;
-                        // owner pixel of the centre (Eq. 5): floor(U / Z), floor(V / Z)
-                        const int rx = (x << 16) + 32768 - nd.x, ryq = (yy << 16) + 32768 - nd.y,
-                                  rzq = (z << 16) + 32768 - nd.z;
-                        const int64_t Z = (int64_t)mz0 * rx + (int64_t)mz1 * ryq + (int64_t)mz2 * rzq;
-                        const int64_t U = (int64_t)mu0 * rx + (int64_t)mu1 * ryq + (int64_t)mu2 * rzq;
-                        const int64_t V = (int64_t)mv0 * rx + (int64_t)mv1 * ryq + (int64_t)mv2 * rzq;
-                        if (Z > 0 && U >= 0 && U < (int64_t)p.W * Z && V >= 0 && V < (int64_t)p.H * Z) {
-                            const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(yy) - Pyf;
-                            const float zi_ = __frcp_rn(fmaf(hz.a, fxr, fmaf(hz.b, fyr, hz.c * rz)));
-                            const float uf = fmaf(hu.a, fxr, fmaf(hu.b, fyr, hu.c * rz)) * zi_;
-                            const float vf = fmaf(hv.a, fxr, fmaf(hv.b, fyr, hv.c * rz)) * zi_;
-                            const int pi = floor_div_from(U, Z, uf, p.W);
-                            const int pj = floor_div_from(V, Z, vf, p.H);
-                            const int man = abs(x - (nd.x >> 16)) + abs(yy - (nd.y >> 16)) + abs(z - (nd.z >> 16));
-                            const int lim = p.steps[(size_t)ql * WH + (size_t)pj * p.W + pi];
-                            if (man <= lim) {
-                                if constexpr (STATS) ++st_visit;
-                                int dx, dy, dz;
-                                ray_dir(p.body[pj * p.W + pi], ck, sk, dx, dy, dz);
-                                counted = visit_index(nd.x, nd.y, nd.z, dx, dy, dz, x, yy, z) >= 0;
-                            }
-                        }
-                    }
+                    const uint32_t addr = ((uint32_t)z * (uint32_t)gny + (uint32_t)(yb + r)) * (uint32_t)gnx + (uint32_t)x;
+                    unk = load_code(p.grid.g, addr, p.grid, p.bounds_err) == kUnknown;
+                    if constexpr (STATS) st_unk += unk;
                 }
-                // counted samples: absolute gain, then the ancestor test in batches of 32 (Sec. IV-B)
-                c_abs += counted;
-                const unsigned bal = __ballot_sync(0xffffffffu, counted);
-                if (bal) {
-                    if (counted)
-                        q[qn + __popc(bal & lt_mask)] = (unsigned long long)x | ((unsigned long long)yy << 16) |
-                                                        ((unsigned long long)z << 32);
-                    qn += __popc(bal);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        const unsigned long long sm = q[lane];
-                        c_mrg += !observed<STATS>(HotDirect{p}, anc, na, (int)(sm & 0xFFFF), (int)((sm >> 16) & 0xFFFF),
-                                                  (int)(sm >> 32), st_anc, st_reads);
-                        __syncwarp();
-                        if (lane < qn - 32) q[lane] = q[lane + 32];
-                        __syncwarp();
-                        qn -= 32;
+                q_push(Q.unk, nu, unk, (unsigned long long)x | ((unsigned long long)(yb + r) << 12), lt_mask);
+                if (nu >= 32) {
+                    owner_stage(true);
+                    if (no >= 32) {
+                        visit_stage(true);
+                        if (ns >= 32) ancestor_stage(true);
                     }
                 }
             }
         }
-        __syncwarp();
-        if (lane < qn) {
-            const unsigned long long sm = q[lane];
-            c_mrg += !observed<STATS>(HotDirect{p}, anc, na, (int)(sm & 0xFFFF), (int)((sm >> 16) & 0xFFFF),
-                                      (int)(sm >> 32), st_anc, st_reads);
+        // the slice's partial batches, stage by stage
+        if (nu > 0) owner_stage(false);
+        while (no >= 32) {
+            visit_stage(true);
+            if (ns >= 32) ancestor_stage(true);
         }
+        if (no > 0) visit_stage(false);
+        while (ns >= 32) ancestor_stage(true);
+        if (ns > 0) ancestor_stage(false);
         c_abs = __reduce_add_sync(0xffffffffu, c_abs);
         c_mrg = __reduce_add_sync(0xffffffffu, c_mrg);
         if (lane == 0 && (c_abs | c_mrg)) {
@@ -236,6 +303,319 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 4) voxel_kernel(const LevelPar
             atomicAdd(p.stats + 11, (unsigned long long)st_cand);
             atomicAdd(p.stats + 12, (unsigned long long)st_unk);
             atomicAdd(p.stats + 13, (unsigned long long)st_visit);
+            atomicAdd(p.stats + 15, (unsigned long long)st_anc);
+            atomicAdd(p.stats + 16, (unsigned long long)st_reads);
+        }
+    }
+}
+
+// Per-warp queues of the per-node pass: unknown voxels of the slice in the band, and counted voxels
+// with the mask of the yaws that count them.
+struct NodeQueues {
+    unsigned long long unk[64];    // x | y << 12
+    unsigned long long key[64];    // x | y << 12 | k_lo << 24 (first yaw of the mask's window)
+    unsigned long long mask[64];   // yaws (from k_lo) that count the voxel
+};
+
+// Stage C of the per-node pass: the ancestor test of 32 (or the last n) counted voxels, then their
+// per-yaw counts: every yaw of the voxel's mask gains an absolute count, and a marginal one unless
+// an ancestor observes the voxel.
+template <bool STATS>
+__device__ __forceinline__ void anc_stage_node(const LevelParams &p, NodeQueues &Q, int &nq, int lane,
+                                               const AncRec *anc, int na, int z, int K, int *s_cnt,
+                                               uint32_t &st_anc, uint32_t &st_reads, uint32_t &st_smp, bool full) {
+    const bool have = full || lane < nq;
+    unsigned long long key, mask;
+    if (full) {
+        key = Q.key[lane];
+        mask = Q.mask[lane];
+        const unsigned long long rk = lane + 32 < nq ? Q.key[lane + 32] : 0ull;
+        const unsigned long long rm = lane + 32 < nq ? Q.mask[lane + 32] : 0ull;
+        __syncwarp();
+        if (lane + 32 < nq) {
+            Q.key[lane] = rk;
+            Q.mask[lane] = rm;
+        }
+        __syncwarp();
+        nq -= 32;
+    } else {
+        key = Q.key[lane];
+        mask = Q.mask[lane];
+        nq = 0;
+    }
+    if (!have) return;
+    const int x = (int)(key & 0xFFF), y = (int)((key >> 12) & 0xFFF);
+    const bool obs = observed<STATS>(HotDirect{p}, anc, na, x, y, z, st_anc, st_reads);
+    int k = (int)(key >> 24);
+    while (mask) {
+        const int j = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        int kk = k + j;
+        kk -= kk >= K ? K : 0;
+        kk -= kk >= K ? K : 0;
+        atomicAdd(s_cnt + 2 * kk, 1);
+        if (!obs) atomicAdd(s_cnt + 2 * kk + 1, 1);
+        if constexpr (STATS) ++st_smp;
+    }
+}
+
+// ------------------------------------------------------------------------ per-node voxel kernel
+// The same counts with each voxel taken once per node for all yaws: the ancestor test of Sec. IV-B
+// does not depend on the node's own yaw, and a voxel lies in several yaws' frusta. Warp work item
+// = (node of the chunk, slice z of its range ball). Stage A: the slice's unknown voxels whose
+// centre's elevation is inside the frustum's band; stage B (one voxel per lane): for every yaw whose
+// frustum may hold it (azimuth window), its owner pixel (Eq. 5), the reach test by step index and
+// the exact visit test, giving a mask of the yaws that count it; stage C: the ancestor test once
+// per counted voxel, then the per-yaw counts in the warp's shared counters (added to the level's
+// counters at the end of the item).
+constexpr int kNodeMaxK = 64;  // yaws of the per-node pass (one mask word, per-warp counters)
+
+// Per-warp state of the per-node pass: queues of unknown voxels in the band and of counted voxels
+// with the mask of the yaws that count them, and the per-yaw (absolute, marginal) counters.
+struct NodeWarp {
+    unsigned long long unk[64];    // x | y << 12
+    unsigned long long key[64];    // x | y << 12 | k_lo << 24 (first yaw of the mask)
+    unsigned long long mask[64];   // yaws (from k_lo, cyclic) that count the voxel
+    int cnt[2 * kNodeMaxK];
+};
+
+// Stage C: the ancestor test of 32 (or the last n) counted voxels, then their per-yaw counts: every
+// yaw of the voxel's mask gains an absolute count, and a marginal one unless an ancestor observes it.
+template <bool STATS>
+__device__ __forceinline__ void node_anc_stage(const LevelParams &p, NodeWarp &Q, int &nq, int lane,
+                                               const AncRec *anc, int na, int z, int K, uint32_t &st_anc,
+                                               uint32_t &st_reads, uint32_t &st_smp, bool full) {
+    const bool have = full || lane < nq;
+    const unsigned long long key = Q.key[lane], mask0 = Q.mask[lane];
+    if (full) {
+        const unsigned long long rk = lane + 32 < nq ? Q.key[lane + 32] : 0ull;
+        const unsigned long long rm = lane + 32 < nq ? Q.mask[lane + 32] : 0ull;
+        __syncwarp();
+        if (lane + 32 < nq) {
+            Q.key[lane] = rk;
+            Q.mask[lane] = rm;
+        }
+        __syncwarp();
+        nq -= 32;
+    } else {
+        nq = 0;
+    }
+    if (have) {
+        const int x = (int)(key & 0xFFF), y = (int)((key >> 12) & 0xFFF);
+        const bool obs = observed<STATS>(HotDirect{p}, anc, na, x, y, z, st_anc, st_reads);
+        const int k0 = (int)(key >> 24);
+        unsigned long long mask = mask0;
+        while (mask) {
+            const int j = __ffsll((long long)mask) - 1;
+            mask &= mask - 1;
+            int kk = k0 + j;
+            kk -= kk >= K ? K : 0;
+            atomicAdd(Q.cnt + 2 * kk, 1);
+            if (!obs) atomicAdd(Q.cnt + 2 * kk + 1, 1);
+            if constexpr (STATS) ++st_smp;
+        }
+    }
+    __syncwarp();
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelParams p) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ NodeWarp s_nw[kVoxWarps];
+    __shared__ int s_yi[kNodeMaxK * 12];    // yaw rows: ck sk mu mv mz -
+    __shared__ float s_yf[kNodeMaxK * 9];   // mu mv mz / 2^16
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int K = p.K;
+    AncRec *anc = reinterpret_cast<AncRec *>(s_dyn) + warp * p.max_anc;
+    NodeWarp &Q = s_nw[warp];
+    const int l0 = p.level_off[p.lvl];
+    const int Ld = p.level_off[p.lvl + 1] - l0;
+    const int nb0 = p.q0 / K, nb1 = min(p.q1 / K, Ld);
+    if (nb0 >= nb1) return;
+    for (int t = threadIdx.x; t < 12 * K; t += blockDim.x) s_yi[t] = p.yawtab[t];
+    for (int t = threadIdx.x; t < 9 * K; t += blockDim.x) s_yf[t] = (float)p.yawtab[(t / 9) * 12 + 2 + t % 9] * (1.0f / 65536.0f);
+    for (int t = lane; t < 2 * K; t += 32) Q.cnt[t] = 0;
+    __syncthreads();
+    const int Rv = (int)(p.Tq >> 16) + 2;
+    const int slices = 2 * Rv + 1;
+    const int nn = nb1 - nb0;
+    const int items = nn * slices;
+    const float R = (float)p.Tq * (1.0f / 65536.0f) + 1.0f, R2 = R * R;
+    const int gnx = p.grid.nx, gny = p.grid.ny, gnz = p.grid.nz;
+    const size_t WH = (size_t)p.W * p.H;
+    const float s16 = 1.0f / 65536.0f, yaw_scale = (float)K * 0.15915494309189535f;  // K / (2 pi)
+    uint32_t st_cand = 0, st_unk = 0, st_visit = 0, st_anc = 0, st_reads = 0, st_smp = 0;
+    int cur_node = -1, na = 0;
+    // items are handed out one at a time from the launch's counter: every node's slice at its own
+    // height first (the fullest), then outwards alternately above and below
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(p.vctr, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int rank = it / nn, ln = it % nn;
+        const int zi = Rv + ((rank & 1) ? (rank + 1) >> 1 : -(rank >> 1));
+        const int n = p.level_nodes[l0 + nb0 + ln];
+        const int4 nd = p.node[n];
+        const int v0x = nd.x >> 16, v0y = nd.y >> 16, v0z = nd.z >> 16;
+        const int z = v0z - Rv + zi;
+        if (z < 0 || z >= gnz) continue;
+        const float Pxf = (float)nd.x * s16 - 0.5f, Pyf = (float)nd.y * s16 - 0.5f, Pzf = (float)nd.z * s16 - 0.5f;
+        const float rz = small_int_to_float(z) - Pzf;
+        const float h2 = R2 - rz * rz;
+        if (h2 < 0.f) continue;
+        // no voxel of this slice can be in the band: above the slice's plane every centre's elevation is
+        // at least that of the outermost one, below it at most that of the outermost one
+        {
+            const float rho_max = sqrtf(h2);
+            const float eps = 0.01f * (rho_max + fabsf(rz)) + 0.05f;
+            if ((rz > 0.f && p.band_thi < 1e29f && rz > p.band_thi * rho_max + eps) ||
+                (rz < 0.f && p.band_tlo > -1e29f && rz < p.band_tlo * rho_max - eps))
+                continue;
+        }
+        if (n != cur_node) {  // the node's ancestors (Sec. IV-B), parent first
+            const int2 ar = p.anc_range[n];
+            na = ar.y;
+            if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
+            else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
+            na = min(na, p.max_anc);
+            fill_anc_records(p, ar, na, anc, lane);
+            cur_node = n;
+        }
+        const uint16_t *steps = p.steps + (size_t)ln * K * WH;
+        const int zq = (z << 16) + 32768 - nd.z;
+        int nu = 0, nq = 0;
+
+        // stage B: for 32 voxels (one per lane), the yaws that count them: every yaw whose frustum may
+        // hold the voxel (azimuth window) in turn
+        auto yaw_stage = [&](bool full) {
+            const bool have = full || lane < nu;
+            const unsigned long long e = full ? q_pop32(Q.unk, nu, lane) : Q.unk[lane];
+            if (!full) nu = 0;
+            const int x = (int)(e & 0xFFF), y = (int)((e >> 12) & 0xFFF);
+            const int rxq = (x << 16) + 32768 - nd.x, ryq = (y << 16) + 32768 - nd.y;
+            const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(y) - Pyf;
+            const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
+            // the yaws whose frustum may hold the centre: psi_k within az_half of its azimuth (every
+            // yaw near the vertical axis)
+            int klo = 0, nk = have ? K : 0;
+            if (have && fxr * fxr + fyr * fyr >= 4.0f && p.az_half < 3.0f) {
+                const float phi = atan2f(fyr, fxr);
+                const int a0 = (int)ceilf((phi - p.az_half) * yaw_scale), a1 = (int)floorf((phi + p.az_half) * yaw_scale);
+                nk = max(0, min(K, a1 - a0 + 1));
+                klo = ((a0 % K) + K) % K;
+            }
+            unsigned long long mask = 0ull;
+            for (int j = 0; j < nk; ++j) {
+                int k = klo + j;
+                k -= k >= K ? K : 0;
+                const int *r = s_yi + 12 * k;
+                const float *f = s_yf + 9 * k;
+                const int64_t Z = (int64_t)r[8] * rxq + (int64_t)r[9] * ryq + (int64_t)r[10] * zq;
+                if (Z <= 0) continue;
+                const int64_t U = (int64_t)r[2] * rxq + (int64_t)r[3] * ryq + (int64_t)r[4] * zq;
+                const int64_t V = (int64_t)r[5] * rxq + (int64_t)r[6] * ryq + (int64_t)r[7] * zq;
+                const float zi_ = __fdividef(1.0f, fmaf(f[6], fxr, fmaf(f[7], fyr, f[8] * rz)));
+                int pu, pv;
+                if (!pixel_in(U, Z, fmaf(f[0], fxr, fmaf(f[1], fyr, f[2] * rz)) * zi_, p.W, pu)) continue;
+                if (!pixel_in(V, Z, fmaf(f[3], fxr, fmaf(f[4], fyr, f[5] * rz)) * zi_, p.H, pv)) continue;
+                const int pix = pv * p.W + pu;
+                if (man >= (int)__ldg(steps + (size_t)k * WH + pix)) continue;  // behind the owner ray's hit
+                if constexpr (STATS) ++st_visit;
+                int dx, dy, dz;
+                ray_dir(p.body[pix], r[0], r[1], dx, dy, dz);
+                if (visit_index(nd.x, nd.y, nd.z, dx, dy, dz, x, y, z, p.Tq) >= 0) mask |= 1ull << j;
+            }
+            const bool put = mask != 0ull;
+            const unsigned bal = __ballot_sync(0xffffffffu, put);
+            if (put) {
+                const int slot = nq + __popc(bal & lt_mask);
+                Q.key[slot] = (unsigned long long)x | ((unsigned long long)y << 12) | ((unsigned long long)klo << 24);
+                Q.mask[slot] = mask;
+            }
+            nq += __popc(bal);
+            __syncwarp();
+            if (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
+        };
+
+        const float hy = sqrtf(h2);
+        const int ylo = max(0, (int)floorf(Pyf - hy) - 1), yhi = min(gny - 1, (int)ceilf(Pyf + hy) + 1);
+        for (int yb = ylo; yb <= yhi; yb += 32) {
+            const int y = yb + lane;
+            int xa = 0, len = 0;
+            if (y <= yhi) {
+                const float ry = small_int_to_float(y) - Pyf;
+                const float hx2 = h2 - ry * ry;
+                if (hx2 >= 0.f) {
+                    const float hx = sqrtf(hx2);
+                    xa = max(0, (int)floorf(Pxf - hx) - 1);
+                    len = max(0, min(gnx - 1, (int)ceilf(Pxf + hx) + 1) - xa + 1);
+                }
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            for (int base = 0; base < tot; base += 32) {
+                const int f = base + lane;
+                int r = 0;
+#pragma unroll
+                for (int sh = 16; sh >= 1; sh >>= 1) {
+                    const int cv = __shfl_sync(0xffffffffu, incl, r + sh - 1);
+                    if (cv <= f) r += sh;
+                }
+                r = min(r, 31);
+                const int rxa = __shfl_sync(0xffffffffu, xa, r);
+                const int rstart = __shfl_sync(0xffffffffu, incl - len, r);
+                bool unk = false;
+                int x = 0;
+                if (f < tot) {
+                    x = rxa + (f - rstart);
+                    if constexpr (STATS) ++st_cand;
+                    const uint32_t addr = ((uint32_t)z * (uint32_t)gny + (uint32_t)(yb + r)) * (uint32_t)gnx + (uint32_t)x;
+                    if (load_code(p.grid.g, addr, p.grid, p.bounds_err) == kUnknown) {
+                        // inside the frustum's elevation band (widened; exact tests follow)
+                        const float fx = small_int_to_float(x) - Pxf, fy = small_int_to_float(yb + r) - Pyf;
+                        const float rho = sqrtf(fx * fx + fy * fy);
+                        const float eps = 0.01f * (rho + fabsf(rz)) + 0.05f;
+                        unk = (p.band_thi >= 1e29f || rz <= p.band_thi * rho + eps) &&
+                              (p.band_tlo <= -1e29f || rz >= p.band_tlo * rho - eps);
+                    }
+                    if constexpr (STATS) st_unk += unk;
+                }
+                q_push(Q.unk, nu, unk, (unsigned long long)x | ((unsigned long long)(yb + r) << 12), lt_mask);
+                if (nu >= 32) yaw_stage(true);
+            }
+        }
+        if (nu > 0) yaw_stage(false);
+        while (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
+        if (nq > 0) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, false);
+        // this slice's counts into the level's counters
+        for (int t = lane; t < 2 * K; t += 32) {
+            const int v = Q.cnt[t];
+            if (v) {
+                atomicAdd(p.cnt + ((size_t)n * K + (t >> 1)) * 2 + (t & 1), v);
+                Q.cnt[t] = 0;
+            }
+        }
+        __syncwarp();
+    }
+    if constexpr (STATS) {
+        st_cand = __reduce_add_sync(0xffffffffu, st_cand);
+        st_unk = __reduce_add_sync(0xffffffffu, st_unk);
+        st_visit = __reduce_add_sync(0xffffffffu, st_visit);
+        st_anc = __reduce_add_sync(0xffffffffu, st_anc);
+        st_reads = __reduce_add_sync(0xffffffffu, st_reads);
+        st_smp = __reduce_add_sync(0xffffffffu, st_smp);
+        if (lane == 0) {
+            atomicAdd(p.stats + 11, (unsigned long long)st_cand);
+            atomicAdd(p.stats + 12, (unsigned long long)st_unk);
+            atomicAdd(p.stats + 13, (unsigned long long)st_visit);
+            atomicAdd(p.stats + 14, (unsigned long long)st_smp);
             atomicAdd(p.stats + 15, (unsigned long long)st_anc);
             atomicAdd(p.stats + 16, (unsigned long long)st_reads);
         }
@@ -296,7 +676,8 @@ size_t steps_pairs(long long pairs, int W, int H, size_t budget_bytes) {
 }
 
 void launch_cast_chunk(const LevelParams &c, int num_sms, cudaStream_t s) {
-    const long long cast_warps = (long long)(c.q1 - c.q0) * ((c.W + 7) / 8) * ((c.H + 3) / 4);
+    const long long cast_warps =
+        (long long)(c.q1 - c.q0) * ((c.W + kCastTileW - 1) / kCastTileW) * ((c.H + kCastTileH - 1) / kCastTileH);
     const int cg = (int)std::max<long long>(1, std::min<long long>((cast_warps + kCastWarps - 1) / kCastWarps,
                                                                     (long long)num_sms * 64));
     if (c.stats) cast_kernel<true><<<cg, kCastWarps * 32, 0, s>>>(c);
@@ -312,13 +693,48 @@ void launch_voxel_chunk(const LevelParams &c, int num_sms, int vox_ctas, cudaStr
     else voxel_kernel<false><<<vg, kVoxWarps * 32, smem, s>>>(c);
 }
 
-void launch_vox_level(const LevelParams &p, long long pairs, int num_sms, int vox_ctas, cudaStream_t s) {
-    for (long long q0 = 0; q0 < pairs; q0 += p.steps_cap) {
+size_t node_dyn_smem(int max_anc) { return (size_t)kVoxWarps * std::max(1, max_anc) * sizeof(AncRec); }
+
+int node_ctas_per_sm() {
+    int a = 0, b = 0;
+    const size_t smem = node_dyn_smem(MIG_MAX_DEPTH);
+    cudaFuncSetAttribute(node_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(node_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, node_kernel<false>, kVoxWarps * 32, node_dyn_smem(16));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, node_kernel<true>, kVoxWarps * 32, node_dyn_smem(16));
+    cudaGetLastError();
+    return std::max(1, std::min(a, b));
+}
+
+// The per-node pass, when it applies: whole nodes in a chunk, at most kNodeMaxK yaws and a frustum
+// band. By default it is taken when a voxel lies in at least 6 yaws' frusta on average (K times the
+// azimuth half-width over pi): below that the per-pair pass runs faster.
+bool node_pass(const LevelParams &p) {
+    if (!(p.az_half > 0.f && p.K <= kNodeMaxK && p.steps_cap >= p.K) || p.voxel_pass == MIG_COUNT_PAIRS) return false;
+    return p.voxel_pass == MIG_COUNT_NODES || (float)p.K * p.az_half >= 6.0f * 3.14159265f;
+}
+
+void launch_node_chunk(const LevelParams &c, int num_sms, int node_ctas, cudaStream_t s) {
+    const int slices = 2 * ((int)(c.Tq >> 16) + 2) + 1;
+    const long long items = (long long)((c.q1 - c.q0) / c.K) * slices;
+    const int g = (int)std::max<long long>(1, std::min<long long>((items + kVoxWarps - 1) / kVoxWarps,
+                                                                   (long long)num_sms * node_ctas));
+    const size_t smem = node_dyn_smem(c.max_anc);
+    if (c.stats) node_kernel<true><<<g, kVoxWarps * 32, smem, s>>>(c);
+    else node_kernel<false><<<g, kVoxWarps * 32, smem, s>>>(c);
+}
+
+int vox_chunk_pairs(const LevelParams &p) { return node_pass(p) ? (p.steps_cap / p.K) * p.K : p.steps_cap; }
+
+void launch_vox_level(const LevelParams &p, long long pairs, int num_sms, int vox_ctas, int node_ctas, cudaStream_t s) {
+    const int cap = vox_chunk_pairs(p);
+    for (long long q0 = 0; q0 < pairs; q0 += cap) {
         LevelParams c = p;
         c.q0 = (int)q0;
-        c.q1 = (int)std::min<long long>(pairs, q0 + p.steps_cap);
+        c.q1 = (int)std::min<long long>(pairs, q0 + cap);
         launch_cast_chunk(c, num_sms, s);
-        launch_voxel_chunk(c, num_sms, vox_ctas, s);
+        if (node_pass(p)) launch_node_chunk(c, num_sms, node_ctas, s);
+        else launch_voxel_chunk(c, num_sms, vox_ctas, s);
     }
 }
 

@@ -46,6 +46,15 @@ MIG_HD bool ev_lt(uint32_t n1, uint32_t a1, int x1, uint32_t n2, uint32_t a2, in
     return l < r || (l == r && x1 < x2);
 }
 
+// a / b in float for a first guess (exact comparisons decide; the device uses the fast division).
+MIG_HD float fast_div(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef((float)a, (float)b);
+#else
+    return (float)a / (float)b;
+#endif
+}
+
 // Number of crossings j in [0, jmax] of an axis (face distances nb + j 2^16, speed adb, index b)
 // that come before the event (NE / AE, e). The caller guarantees that crossing jmax does not, so
 // the answer is at most jmax. tE = NE / AE in float gives a first guess; exact comparisons fix it.
@@ -59,31 +68,22 @@ MIG_HD int crossings_before(uint32_t nb, uint32_t adb, int b, int jmax, uint32_t
     return j;
 }
 
-// Per-axis start of a ray: voxel v, step sign s, face distance n (Q16), speed ad (Q30), and the
-// number of crossings `allowed` along this axis that stay inside the grid and start before the
-// range (the same face limits as axis_init). An axis with d = 0 never crosses.
-MIG_HD void cast_axis(int P, int d, int N, int64_t Tq, int &v, uint32_t &n, uint32_t &ad, int &s,
-                                          int &allowed) {
-    v = P >> 16;
-    int grid_rem;
+// "No occupied voxel within range": larger than every step index (at most 3 * 1027).
+constexpr uint32_t kNoHit = 0xFFFF;
+
+// Per-axis start of a ray from P (Q16) along d (Q30): voxel v0, step sign s, face distance n0 of the
+// first crossing (Q16) and speed ad = |d| (Q30). An axis with d = 0 gets s = 1 and never crosses.
+MIG_HD void ray_axis(int P, int d, int &v0, int &s, uint32_t &n0, uint32_t &ad) {
+    v0 = P >> 16;
     if (d < 0) {
         s = -1;
         ad = (uint32_t)(-d);
-        n = (uint32_t)(P - (v << 16));
-        grid_rem = v;
+        n0 = (uint32_t)(P - (v0 << 16));
     } else {
         s = 1;
         ad = (uint32_t)d;
-        n = (uint32_t)(((v + 1) << 16) - P);
-        grid_rem = N - 1 - v;
-        if (d == 0) {
-            allowed = 0;
-            return;
-        }
+        n0 = (uint32_t)(((v0 + 1) << 16) - P);
     }
-    const uint64_t lim = ((uint64_t)Tq * ad + ((1ull << 30) - 1)) >> 30;  // n >= lim  <=>  t >= T
-    const int64_t range_rem = (n >= lim) ? 0 : (int64_t)((lim - n + (kQ16 - 1)) >> 16);
-    allowed = (int)min((int64_t)grid_rem, range_rem);
 }
 
 // The first of three axis events (n_a / ad_a, a) in event order; axes with ad = 0 never win
@@ -95,104 +95,132 @@ MIG_HD int ev_argmin3(uint32_t n0, uint32_t a0, uint32_t n1, uint32_t a1, uint32
     return bz ? 2 : (xly ? 0 : 1);
 }
 
-// DDA steps a ray takes before it stops: the index (0 = the start voxel) of the first occupied
-// voxel it visits, else of the last voxel it visits before leaving the grid or reaching the range.
-// `fine` and `skips` count voxel steps and brick jumps (statistics).
+// Crossing index (from the start, 0-based) of the crossing that leaves the 8-voxel brick of voxel v
+// along an axis with step s: the brick's last voxel in the direction of travel, or the grid's.
+MIG_HD int brick_exit_crossing(int v, int v0, int s, int N) {
+    return s > 0 ? min(v | 7, N - 1) - v0 : v0 - (v & ~7);
+}
+
+// Crossings an axis may take: those that stay inside the grid and start before the range T (the
+// k-th crossing, k = 0, 1, ..., is at face distance n0 + k 2^16, i.e. at t = (n0 + k 2^16) / ad).
+MIG_HD int allowed_crossings(int v0, int s, uint32_t n0, uint32_t ad, int N, int64_t Tq) {
+    if (ad == 0) return 0;
+    const int grid_rem = s > 0 ? N - 1 - v0 : v0;
+    const uint64_t lim = ((uint64_t)Tq * ad + ((1ull << 30) - 1)) >> 30;  // n >= lim  <=>  t >= T
+    const int64_t range_rem = (n0 >= lim) ? 0 : (int64_t)((lim - n0 + (kQ16 - 1)) >> 16);
+    return (int)min((int64_t)grid_rem, range_rem);
+}
+
+// Step index of the first occupied voxel that the DDA (Sec. IV-B) visits, else kNoHit: the ray
+// stops on that voxel and visits no voxel beyond it. A voxel is visited iff its entering crossing
+// is allowed (inside the grid, before the range T); per axis the allowed crossings are a prefix
+// of its crossings, so each step compares one crossing index (or face distance) with a limit
+// fixed at the start. Bricks without an occupied voxel are crossed by a brick-level walk whose
+// crossings are exactly the brick faces of the voxel walk, in the same order; on entering a brick
+// with an occupied voxel the voxel state there is rebuilt exactly from the start (per axis, the
+// crossings that precede the entering event) and the voxel walk continues. `fine` and `coarse`
+// count voxel and brick steps (statistics).
 template <bool STATS>
-MIG_HD uint32_t cast_steps(const uint8_t *g, const uint8_t *bocc, int gnx, int gny, int gnz,
-                                               int Px, int Py, int Pz, int dx, int dy, int dz, int64_t Tq,
-                                               uint32_t &fine, uint32_t &skips) {
-    int vx, vy, vz, sx, sy, sz, cx, cy, cz;
-    uint32_t nx, ny, nz, ax, ay, az;
-    cast_axis(Px, dx, gnx, Tq, vx, nx, ax, sx, cx);
-    cast_axis(Py, dy, gny, Tq, vy, ny, ay, sy, cy);
-    cast_axis(Pz, dz, gnz, Tq, vz, nz, az, sz, cz);
-    // the first disallowed crossing of each axis is at n + allowed 2^16; the earliest of them ends
-    // the ray, after m_end allowed crossings
-    uint32_t m_end;
-    {
-        const uint32_t Lx = nx + ((uint32_t)cx << 16), Ly = ny + ((uint32_t)cy << 16), Lz = nz + ((uint32_t)cz << 16);
-        const int e = ev_argmin3(Lx, ax, Ly, ay, Lz, az);
-        const uint32_t NE = e == 0 ? Lx : (e == 1 ? Ly : Lz), AE = e == 0 ? ax : (e == 1 ? ay : az);
-        const float tE = (float)NE / (float)AE;
-        m_end = (uint32_t)((e == 0 ? cx : crossings_before(nx, ax, 0, cx, NE, AE, e, tE)) +
-                           (e == 1 ? cy : crossings_before(ny, ay, 1, cy, NE, AE, e, tE)) +
-                           (e == 2 ? cz : crossings_before(nz, az, 2, cz, NE, AE, e, tE)));
-    }
+MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, int gnx, int gny, int gnz, int Px, int Py, int Pz,
+                         int dx, int dy, int dz, int64_t Tq, uint32_t &fine, uint32_t &coarse) {
+    int v0x, v0y, v0z, sx, sy, sz;
+    uint32_t n0x, n0y, n0z, ax, ay, az;
+    ray_axis(Px, dx, v0x, sx, n0x, ax);
+    ray_axis(Py, dy, v0y, sy, n0y, ay);
+    ray_axis(Pz, dz, v0z, sz, n0z, az);
+    const int kx = allowed_crossings(v0x, sx, n0x, ax, gnx, Tq), ky = allowed_crossings(v0y, sy, n0y, ay, gny, Tq),
+              kz = allowed_crossings(v0z, sz, n0z, az, gnz, Tq);
+    // face limits: a crossing at face distance n along an axis is allowed iff n < l
+    const uint32_t lx = n0x + ((uint32_t)kx << 16), ly = n0y + ((uint32_t)ky << 16), lz = n0z + ((uint32_t)kz << 16);
     const int nbx = (gnx + 7) >> 3, nby = (gny + 7) >> 3;
     const int dax = sx, day = sy * gnx, daz = sz * gnx * gny;
-    uint32_t addr = ((uint32_t)vz * (uint32_t)gny + (uint32_t)vy) * (uint32_t)gnx + (uint32_t)vx;
-    uint32_t m = 0;
-    int cur = -1;
-    bool occ = true;
+    // voxel state (valid in the voxel walk): current voxel, next crossing per axis, step index
+    int vx = v0x, vy = v0y, vz = v0z;
+    uint32_t nx = n0x, ny = n0y, nz = n0z, m = 0;
     for (;;) {
-        if (bocc) {
-            const int bi = ((vz >> 3) * nby + (vy >> 3)) * nbx + (vx >> 3);
-            if (bi != cur) {
-                cur = bi;
-                occ = ld_u8(bocc + bi) != 0;
+        if (!bocc || ld_u8(bocc + ((vz >> 3) * nby + (vy >> 3)) * nbx + (vx >> 3))) {
+            // voxel walk inside a brick that holds an occupied voxel, up to its faces: bnx.. = face
+            // distance of the crossing that leaves the brick along each axis
+            const uint32_t bnx = n0x + ((uint32_t)brick_exit_crossing(vx, v0x, sx, gnx) << 16);
+            const uint32_t bny = n0y + ((uint32_t)brick_exit_crossing(vy, v0y, sy, gny) << 16);
+            const uint32_t bnz = n0z + ((uint32_t)brick_exit_crossing(vz, v0z, sz, gnz) << 16);
+            uint32_t addr = ((uint32_t)vz * (uint32_t)gny + (uint32_t)vy) * (uint32_t)gnx + (uint32_t)vx;
+            for (;;) {
+                if constexpr (STATS) ++fine;
+                if (ld_u8(g + addr) == kOcc) return m;
+                const int a = ev_argmin3(nx, ax, ny, ay, nz, az);
+                const uint32_t na = a == 0 ? nx : (a == 1 ? ny : nz);
+                if (na >= (a == 0 ? lx : (a == 1 ? ly : lz))) return kNoHit;  // leaves the grid or the range
+                const bool leave = na == (a == 0 ? bnx : (a == 1 ? bny : bnz));
+                nx += a == 0 ? kQ16 : 0u;
+                ny += a == 1 ? kQ16 : 0u;
+                nz += a == 2 ? kQ16 : 0u;
+                vx += a == 0 ? sx : 0;
+                vy += a == 1 ? sy : 0;
+                vz += a == 2 ? sz : 0;
+                addr += a == 0 ? dax : (a == 1 ? day : daz);
+                ++m;
+                if (leave) break;  // entered another brick
             }
-        }
-        if (!occ) {
-            // no occupied voxel in this brick: jump to the crossing that leaves it (exact)
-            const int rx = ax == 0 ? 0 : (sx > 0 ? min(vx | 7, gnx - 1) - vx : vx & 7);
-            const int ry = ay == 0 ? 0 : (sy > 0 ? min(vy | 7, gny - 1) - vy : vy & 7);
-            const int rz = az == 0 ? 0 : (sz > 0 ? min(vz | 7, gnz - 1) - vz : vz & 7);
-            const uint32_t Nx = nx + ((uint32_t)rx << 16), Ny = ny + ((uint32_t)ry << 16), Nz = nz + ((uint32_t)rz << 16);
-            const int e = ev_argmin3(Nx, ax, Ny, ay, Nz, az);
-            const uint32_t NX = e == 0 ? Nx : (e == 1 ? Ny : Nz), AX = e == 0 ? ax : (e == 1 ? ay : az);
-            const float tX = (float)NX / (float)AX;
-            const int kx = e == 0 ? rx + 1 : crossings_before(nx, ax, 0, rx, NX, AX, e, tX);
-            const int ky = e == 1 ? ry + 1 : crossings_before(ny, ay, 1, ry, NX, AX, e, tX);
-            const int kz = e == 2 ? rz + 1 : crossings_before(nz, az, 2, rz, NX, AX, e, tX);
-            const uint32_t tot = (uint32_t)(kx + ky + kz);
-            if constexpr (STATS) ++skips;
-            if (m + tot >= m_end) return m_end;  // the ray ends inside this brick (or just after it)
-            m += tot;
-            nx += (uint32_t)kx << 16;
-            ny += (uint32_t)ky << 16;
-            nz += (uint32_t)kz << 16;
-            vx += sx * kx;
-            vy += sy * ky;
-            vz += sz * kz;
-            addr = ((uint32_t)vz * (uint32_t)gny + (uint32_t)vy) * (uint32_t)gnx + (uint32_t)vx;
             continue;
         }
-        if constexpr (STATS) ++fine;
-        if (ld_u8(g + addr) == kOcc) return m;
-        if (m == m_end) return m;
-        const int a = ev_argmin3(nx, ax, ny, ay, nz, az);
-        nx += a == 0 ? kQ16 : 0u;
-        ny += a == 1 ? kQ16 : 0u;
-        nz += a == 2 ? kQ16 : 0u;
-        vx += a == 0 ? sx : 0;
-        vy += a == 1 ? sy : 0;
-        vz += a == 2 ? sz : 0;
-        addr += a == 0 ? dax : (a == 1 ? day : daz);
-        ++m;
+        // brick walk: per axis the crossing index (from the start) that leaves the current brick
+        int ex = brick_exit_crossing(vx, v0x, sx, gnx), ey = brick_exit_crossing(vy, v0y, sy, gny),
+            ez = brick_exit_crossing(vz, v0z, sz, gnz);
+        int bx = vx >> 3, by = vy >> 3, bz = vz >> 3;
+        for (;;) {
+            if constexpr (STATS) ++coarse;
+            const uint32_t Nx = n0x + ((uint32_t)ex << 16), Ny = n0y + ((uint32_t)ey << 16), Nz = n0z + ((uint32_t)ez << 16);
+            const int e = ev_argmin3(Nx, ax, Ny, ay, Nz, az);
+            const int Ee = e == 0 ? ex : (e == 1 ? ey : ez);
+            if (Ee >= (e == 0 ? kx : (e == 1 ? ky : kz))) return kNoHit;  // leaves the grid or the range
+            const uint32_t NE = e == 0 ? Nx : (e == 1 ? Ny : Nz), AE = e == 0 ? ax : (e == 1 ? ay : az);
+            // the voxel that crossing enters along e, and the brick beyond
+            const int s_e = e == 0 ? sx : (e == 1 ? sy : sz), v0e = e == 0 ? v0x : (e == 1 ? v0y : v0z);
+            const int ue = v0e + s_e * (Ee + 1);
+            const int nb = ue >> 3;
+            const int nEe = brick_exit_crossing(ue, v0e, s_e, e == 0 ? gnx : (e == 1 ? gny : gnz));
+            bx = e == 0 ? nb : bx;
+            by = e == 1 ? nb : by;
+            bz = e == 2 ? nb : bz;
+            ex = e == 0 ? nEe : ex;
+            ey = e == 1 ? nEe : ey;
+            ez = e == 2 ? nEe : ez;
+            if (ld_u8(bocc + (bz * nby + by) * nbx + bx)) {
+                // enter it: the voxel state after the entering event (NE, AE, e), from the start; the
+                // other axes' next brick faces (ex, ey, ez) come after that event
+                const float tE = fast_div(NE, AE);
+                const int cx = e == 0 ? Ee + 1 : crossings_before(n0x, ax, 0, ex, NE, AE, e, tE);
+                const int cy = e == 1 ? Ee + 1 : crossings_before(n0y, ay, 1, ey, NE, AE, e, tE);
+                const int cz = e == 2 ? Ee + 1 : crossings_before(n0z, az, 2, ez, NE, AE, e, tE);
+                vx = v0x + sx * cx;
+                vy = v0y + sy * cy;
+                vz = v0z + sz * cz;
+                nx = n0x + ((uint32_t)cx << 16);
+                ny = n0y + ((uint32_t)cy << 16);
+                nz = n0z + ((uint32_t)cz << 16);
+                m = (uint32_t)(cx + cy + cz);
+                break;
+            }
+        }
     }
 }
 
-// Does the DDA of the ray from P (Q16) along d (Q30) visit voxel (x, y, z), and after how many
-// steps? The voxel lies c_a = s_a (v_a - v0_a) crossings from the start voxel along each axis; it
-// is visited iff every c_a >= 0 (c_a = 0 where d_a = 0) and its last entering event precedes its
-// first leaving event. Returns the step index (c_x + c_y + c_z), or -1 if never visited.
-MIG_HD int visit_index(int Px, int Py, int Pz, int dx, int dy, int dz, int x, int y, int z) {
+// Does the DDA of the ray from P (Q16) along d (Q30) reach voxel (x, y, z) before the range T, and
+// after how many steps? The voxel lies c_a = s_a (v_a - v0_a) crossings from the start voxel along
+// each axis; it is on the ray iff every c_a >= 0 (c_a = 0 where d_a = 0) and its last entering
+// event precedes its first leaving event, and it is reached iff that entering event starts before
+// T. Returns the step index c_x + c_y + c_z, or -1. (The grid needs no test for a voxel inside it:
+// the voxels between the start and it are inside too.)
+MIG_HD int visit_index(int Px, int Py, int Pz, int dx, int dy, int dz, int x, int y, int z, int64_t Tq) {
     uint32_t n[3], ad[3];
     int c[3];
     const int P[3] = {Px, Py, Pz}, d[3] = {dx, dy, dz}, v[3] = {x, y, z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int v0 = P[a] >> 16;
-        if (d[a] < 0) {
-            ad[a] = (uint32_t)(-d[a]);
-            n[a] = (uint32_t)(P[a] - (v0 << 16));
-            c[a] = v0 - v[a];
-        } else {
-            ad[a] = (uint32_t)d[a];
-            n[a] = (uint32_t)(((v0 + 1) << 16) - P[a]);
-            c[a] = v[a] - v0;
-        }
+        int v0, s;
+        ray_axis(P[a], d[a], v0, s, n[a], ad[a]);
+        c[a] = s * (v[a] - v0);
         if (c[a] < 0 || (ad[a] == 0 && c[a] != 0)) return -1;
     }
     // last entering event: crossing c_a - 1 of each axis with c_a >= 1
@@ -210,6 +238,7 @@ MIG_HD int visit_index(int Px, int Py, int Pz, int dx, int dy, int dz, int x, in
         }
     }
     if (ea < 0) return 0;  // the start voxel
+    if (((uint64_t)en << 30) >= (uint64_t)Tq * eA) return -1;  // entered at t >= T
     // first leaving event: crossing c_a of each axis that moves
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

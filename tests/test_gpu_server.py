@@ -6,6 +6,7 @@ import threading
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from synth import Sensor
 
@@ -87,6 +88,58 @@ def test_map_updates_keep_snapshots(ctx):
         srv.close()
     assert np.array_equal(m.read(), grids[-1])  # the map ends with every update applied
     m.close()
+
+
+def test_map_snapshots_count_against_the_budget(ctx):
+    """Requests and map updates interleaved on one map. An update that arrives while requests read
+    the map's grid copies it (the requests keep the old one); that copy counts against the budget
+    like the requests' own bytes. With a budget below one request plus a grid copy, the update waits
+    for the request to finish instead of copying: the server's peak holding stays exactly one
+    request's bytes. With a large budget the server may copy. Every result equals the oracle on the
+    map as submitted, and nothing is held at the end."""
+    rng = np.random.default_rng(9)
+    base = synth.random_small(71, nx=48, ny=40, nz=16, n_nodes=12, max_depth=4)
+    g0 = base.map.grid.copy()
+    nz, ny, nx = g0.shape
+    updates, grids, g = [], [g0], g0
+    for i in range(4):
+        box = rng.integers(0, 3, size=(nz, ny // 2, nx // 2)).astype(np.uint8)
+        x0, y0 = int(rng.integers(0, nx - nx // 2)), int(rng.integers(0, ny - ny // 2))
+        updates.append((x0, y0, box))
+        g = g.copy()
+        g[:, y0:y0 + ny // 2, x0:x0 + nx // 2] = box
+        grids.append(g)
+    refs = [oracle.eval_tree(gi, base.map.voxel_size, base.map.origin, base.tree.parent, base.tree.pos, base.sensor)
+            for gi in grids]
+
+    def serve(budget, n_grids):
+        m = mig.Map(ctx, g0, base.map.voxel_size, base.map.origin)
+        srv = mig.Server(ctx, arena_budget_bytes=budget, max_inflight=8)
+        subs = []
+        try:
+            for i in range(n_grids):
+                subs.append((srv.submit(m, base.tree.parent, base.tree.pos, base.sensor), i))
+                subs.append((srv.submit(m, base.tree.parent, base.tree.pos, base.sensor), i))
+                if i < n_grids - 1:
+                    x0, y0, box = updates[i]
+                    srv.map_update(m, x0, y0, 0, box)
+            for (t, out), gi in subs:
+                assert srv.poll(t, timeout_us=60_000_000)
+                for k in ("abs", "marg", "yaw"):
+                    assert np.array_equal(out[k], refs[gi][k]), (budget, gi, k)
+            mem = srv.memory()
+        finally:
+            srv.close()
+            m.close()
+        return mem
+
+    alone = serve(1, 1)  # budget 1: one request at a time; this run has no update
+    one_request = alone["peak"]
+    assert one_request > 0
+    tight = serve(1, len(grids))
+    assert tight["peak"] == one_request and tight["snapshots"] == 0 and tight["in_use"] == 0
+    big = serve(1 << 30, len(grids))
+    assert big["snapshots"] == 0 and big["in_use"] == 0 and big["peak"] >= one_request
 
 
 def test_tight_budget_and_threads(ctx):

@@ -25,7 +25,7 @@ KEYS = ("abs", "marg", "yaw", "cnt_abs", "cnt_marg", "depth")
 def ctx():
     c = mig.Context(0)
     yield c
-    c.set_count_kernel(False, 0)
+    c.set_count_kernel(mig.COUNT_AUTO, 0)
     c.close()
 
 
@@ -54,16 +54,27 @@ def _oracle(p, grid=None, mode=0, depth=True):
                             want_counts=True, want_depth=depth)
 
 
+# includes frusta that hold the vertical (looking steeply down, and nearly straight up: every yaw
+# may hold a voxel), steep pitch, a 1x1 image, a wide and flat image, and more yaws than the
+# per-node pass caches in shared memory (130)
 SENSORS = [None, Sensor(87, 58, 48, 28, 2.0, 12, 10.0), Sensor(60, 45, 33, 17, 3.0, 5, -20.0),
-           Sensor(120, 90, 7, 5, 2.5, 3, 0.0), Sensor(90, 60, 1, 1, 2.0, 4, 0.0), Sensor(170, 20, 61, 9, 2.2, 7, 35.0)]
+           Sensor(120, 90, 7, 5, 2.5, 3, 0.0), Sensor(90, 60, 1, 1, 2.0, 4, 0.0), Sensor(170, 20, 61, 9, 2.2, 7, 35.0),
+           Sensor(100, 150, 21, 17, 2.5, 9, 50.0), Sensor(60, 40, 15, 11, 2.0, 24, -80.0),
+           Sensor(30, 20, 16, 12, 3.0, 130, 0.0)]
 
 
+@pytest.mark.parametrize("voxel_pass", [mig.COUNT_PAIRS, mig.COUNT_NODES])
 @pytest.mark.parametrize("si", range(len(SENSORS)))
 @pytest.mark.parametrize("mode", [mig.MODE_MARGINAL, mig.MODE_SINGLE_PARENT, mig.MODE_ABSOLUTE])
-def test_owned_voxel_count_bit_exact(ctx, si, mode):
-    ctx.set_count_kernel(False, 0)
-    p = synth.random_small(300 + si, n_nodes=14, max_depth=5, sensor=SENSORS[si])
-    _same(_eval(ctx, p, mode=mode), _oracle(p, mode=mode), what=f"sensor {si} mode {mode}")
+def test_owned_voxel_count_bit_exact(ctx, si, mode, voxel_pass):
+    """Both owned-voxel passes (per (node, yaw) frustum and per node over all yaws; the per-node
+    pass takes at most 64 yaws and falls back to the per-pair one above that)."""
+    ctx.set_count_kernel(voxel_pass, 0)
+    try:
+        p = synth.random_small(300 + si, n_nodes=14, max_depth=5, sensor=SENSORS[si])
+        _same(_eval(ctx, p, mode=mode), _oracle(p, mode=mode), what=f"sensor {si} mode {mode} pass {voxel_pass}")
+    finally:
+        ctx.set_count_kernel(mig.COUNT_AUTO, 0)
 
 
 @pytest.mark.parametrize("seed", [11, 12, 13])
@@ -73,16 +84,31 @@ def test_many_chunks_per_level(ctx, seed):
     p = synth.random_small(seed, n_nodes=24, max_depth=4)
     s = p.sensor
     try:
-        ctx.set_count_kernel(False, 3 * s.width * s.height * 2)
+        ctx.set_count_kernel(mig.COUNT_PAIRS, 3 * s.width * s.height * 2)
         got = _eval(ctx, p)
     finally:
-        ctx.set_count_kernel(False, 0)
+        ctx.set_count_kernel(mig.COUNT_AUTO, 0)
     _same(got, _oracle(p), what="3-pair chunks")
 
 
+@pytest.mark.parametrize("seed", [14, 15])
+def test_node_chunks(ctx, seed):
+    """A step-count buffer of two nodes' pairs (all their yaws): the per-node voxel pass runs over
+    many chunks of whole nodes per level."""
+    p = synth.random_small(seed, n_nodes=24, max_depth=4)
+    s = p.sensor
+    try:
+        ctx.set_count_kernel(mig.COUNT_NODES, 2 * s.yaw_bins * s.width * s.height * 2)
+        got = _eval(ctx, p)
+    finally:
+        ctx.set_count_kernel(mig.COUNT_AUTO, 0)
+    _same(got, _oracle(p), what="two-node chunks")
+
+
 def test_tiny_and_sampled_paper_scale_against_ray_by_ray(ctx):
-    """The owned-voxel and ray-by-ray count kernels agree on the tiny workload and on the nodes of depth
-    <= 3 of the paper-scale tree (host-array path), and the tiny workload equals the oracle."""
+    """The two owned-voxel passes and the ray-by-ray count kernel agree on the tiny workload and on the
+    nodes of depth <= 3 of the paper-scale tree (host-array path), and the tiny workload equals the
+    oracle."""
     for p in (synth.tiny(), synth.paper_scale()):
         d = p.tree.depth()
         keep = np.nonzero(d <= (10 if p.name == "tiny" else 3))[0]
@@ -90,12 +116,14 @@ def test_tiny_and_sampled_paper_scale_against_ray_by_ray(ctx):
         remap[keep] = np.arange(keep.size)
         par = np.where(p.tree.parent[keep] >= 0, remap[p.tree.parent[keep]], -1).astype(np.int32)
         sub = synth.Problem(p.name, p.map, synth.Tree(par, p.tree.pos[keep]), p.sensor)
-        ctx.set_count_kernel(False, 0)
-        a = _eval(ctx, sub, depth=False)
-        ctx.set_count_kernel(True, 0)
-        b = _eval(ctx, sub, depth=False)
-        ctx.set_count_kernel(False, 0)
-        _same(a, b, keys=("abs", "marg", "yaw", "cnt_abs", "cnt_marg"), what=p.name)
+        outs = []
+        for kern in (mig.COUNT_PAIRS, mig.COUNT_NODES, mig.COUNT_RAYS):
+            ctx.set_count_kernel(kern, 0)
+            outs.append(_eval(ctx, sub, depth=False))
+        ctx.set_count_kernel(mig.COUNT_AUTO, 0)
+        a = outs[0]
+        for b in outs[1:]:
+            _same(a, b, keys=("abs", "marg", "yaw", "cnt_abs", "cnt_marg"), what=p.name)
         if p.name == "tiny":
             _same(a, _oracle(sub, depth=False), keys=("abs", "marg", "yaw", "cnt_abs", "cnt_marg"), what="tiny")
 
@@ -103,7 +131,7 @@ def test_tiny_and_sampled_paper_scale_against_ray_by_ray(ctx):
 def test_map_updates_refresh_brick_occupancy(ctx):
     """Updates that fill a free region with occupied voxels and clear occupied ones: the brick summary
     follows, so results equal the oracle on the updated grid after every update."""
-    ctx.set_count_kernel(False, 0)
+    ctx.set_count_kernel(mig.COUNT_AUTO, 0)
     rng = np.random.default_rng(5)
     p = synth.random_small(21, nx=40, ny=36, nz=20, n_nodes=16, max_depth=4, sensor=Sensor(90, 60, 24, 16, 3.0, 6, 0.0))
     g = p.map.grid.copy()
@@ -125,7 +153,7 @@ def test_map_updates_refresh_brick_occupancy(ctx):
 def test_stats_agree_between_kernels(ctx):
     """The instrumented pass re-runs the ray-by-ray kernel beside the owned-voxel one: both count the
     same samples, and the cast covers every ray."""
-    ctx.set_count_kernel(False, 0)
+    ctx.set_count_kernel(mig.COUNT_AUTO, 0)
     p = synth.tiny()
     m = mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin)
     try:

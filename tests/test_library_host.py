@@ -34,6 +34,15 @@ def test_library_exports_every_declared_symbol(mig):
     assert sorted(mig.EXPORTS) == names
 
 
+def test_libraries_resolve_every_symbol_at_load(mig):
+    """Both builds (the library and the bounds-checked one) load with immediate binding: no symbol
+    of the library's own code is left undefined."""
+    import ctypes
+    from paper_2609_40297_gb300 import _build
+    for path in (_build.build(), _build.build(checked=True)):
+        ctypes.CDLL(path, mode=os.RTLD_NOW)
+
+
 def test_resolution_rule_golden(mig):
     """Sec. IV-A: W_D = ceil(2 d_max tan(theta_h/2) / v), H_D likewise (tests/golden)."""
     rows = [ln.split() for ln in open(os.path.join(ROOT, "tests", "golden", "resolution_rule.txt"))

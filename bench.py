@@ -758,8 +758,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="headline: skip the batched and serving parts")
     ap.add_argument("--serve-rate-hz", type=float, default=20.0, help="serving: Poisson request rate per robot")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
-                    help="serving: arrival window (the workload specifies 30 s; at 20 Hz per robot the queue grows
-                         "by ~280 requests per second, so the default run replays the first 3 s)")
+                    help="serving: arrival window (the workload specifies 30 s; at 20 Hz per robot the queue "
+                         "grows by ~280 requests per second, so the default run replays the first 3 s)")
     ap.add_argument("--batch-repeats", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -148,6 +148,7 @@ def spread(xs):
 KERNEL_SOURCES = {
     "cast_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
     "voxel_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
+    "node_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
     "count_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
     "render_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
 }
@@ -191,7 +192,7 @@ def kernel_units(kernel, st):
     if kernel == "cast_kernel":
         return (st["cast_steps"] + st["cast_jumps"] + 18 * st["cast_rays"],
                 "voxel steps + brick jumps (1 B each) + cast rays (16 B ray entry + 2 B step count)")
-    if kernel == "voxel_kernel":
+    if kernel in ("voxel_kernel", "node_kernel"):
         return (st["voxel_candidates"] + 18 * st["owned_samples"] + 4 * st["voxel_depth_reads"],
                 "enumerated voxels (1 B) + counted samples (2 B step count + 16 B ray entry) + depth reads (4 B)")
     if kernel == "count_kernel":
@@ -312,7 +313,8 @@ def measure_single(workload, steps, warmup, with_modes=False):
     # time, against the measured HBM copy bandwidth
     kms = {k: ktimes[f"{k}_ms"] for k in ("cast", "voxel", "count", "render")}
     dom = max(kms, key=kms.get)
-    kernel = f"{dom}_kernel"
+    # the voxel kind times whichever voxel pass ran: per (node, yaw) pair or per node
+    kernel = "node_kernel" if dom == "voxel" and stats.get("voxel_pass") == 3 else f"{dom}_kernel"
     launches = max(1, int(ktimes[f"{dom}_launches"]))
     lps = launches / steps
     avg_launch_s = kms[dom] / 1e3 / launches

@@ -350,6 +350,8 @@ typedef struct mig_eval_stats {
      * ancestor tests and depth reads of those samples */
     uint64_t cast_rays, cast_steps, cast_jumps, voxel_candidates, voxel_unknown, visit_tests, owned_samples;
     uint64_t voxel_ancestor_tests, voxel_depth_reads;
+    /* the voxel pass that ran: MIG_COUNT_PAIRS or MIG_COUNT_NODES (MIG_COUNT_RAYS when counting ray by ray) */
+    uint64_t voxel_pass;
 } mig_eval_stats;
 mig_status mig_tree_eval_stats(mig_map *map, int n, const int32_t *parent, const float *pos_m,
                                const mig_sensor *sensor, mig_eval_stats *stats, int32_t *abs_gain,

@@ -86,7 +86,7 @@ class EvalStats(C.Structure):
                                           "depth_reads", "render_rays", "render_steps", "count_launches",
                                           "render_launches", "cast_rays", "cast_steps", "cast_jumps",
                                           "voxel_candidates", "voxel_unknown", "visit_tests", "owned_samples",
-                                          "voxel_ancestor_tests", "voxel_depth_reads")]
+                                          "voxel_ancestor_tests", "voxel_depth_reads", "voxel_pass")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -714,6 +714,7 @@ static mig_status eval_host(mig_map *m, int n, const int32_t *parent, const floa
         stats->owned_samples = st8[14];
         stats->voxel_ancestor_tests = st8[15];
         stats->voxel_depth_reads = st8[16];
+        stats->voxel_pass = !p.steps ? MIG_COUNT_RAYS : (node_pass(p) ? MIG_COUNT_NODES : MIG_COUNT_PAIRS);
     }
     return MIG_OK;
 }

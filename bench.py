@@ -240,9 +240,15 @@ def init_dist(local):
 
 
 # ----------------------------------------------------------------------------- one tree
-def measure_single(workload, steps, warmup, with_modes=False):
+COUNT_PASSES = {"auto": 0, "rays": 1, "pairs": 2, "nodes": 3}
+
+
+def measure_single(workload, steps, warmup, with_modes=False, count_pass="auto", first_nodes=0):
     """Times `steps` whole-tree evaluations of one workload on the device-resident path (after
-    `warmup`), then the host-array path end to end; returns the benchmark's fields."""
+    `warmup`), then the host-array path end to end; returns the benchmark's fields. `count_pass`
+    picks the counting kernels (auto: the library's choice; rays: ray by ray; pairs / nodes: the
+    owned-voxel pass per (node, yaw) or per node). `first_nodes` > 0 keeps only the tree's first nodes
+    (parents precede children, so they form a sub-tree): a smaller case of the same kernels."""
     import torch
 
     import paper_2609_40297_gb300 as mig
@@ -251,11 +257,16 @@ def measure_single(workload, steps, warmup, with_modes=False):
     ws, rank, local = dist_env()
     dev = init_dist(local)
     prob = make_problem(workload, rank)
+    desc = WORKLOAD_DESC[workload]
+    if 0 < first_nodes < prob.tree.n:
+        prob.tree = synth.Tree(prob.tree.parent[:first_nodes].copy(), prob.tree.pos[:first_nodes].copy())
+        desc += f" (its first {first_nodes} nodes)"
     s = prob.sensor
     n = prob.tree.n
     max_depth = int(prob.tree.depth().max())
     rays_per_step = n * s.yaw_bins * s.width * s.height
     ctx = mig.Context(local)
+    ctx.set_count_kernel(COUNT_PASSES[count_pass])
     stream = torch.cuda.current_stream(dev)
     m = mig.Map(ctx, prob.map.grid, prob.map.voxel_size, prob.map.origin)
     par = torch.from_numpy(prob.tree.parent).to(dev)
@@ -331,10 +342,11 @@ def measure_single(workload, steps, warmup, with_modes=False):
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": warmup,
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE, "data": DATA,
-        "config": {"workload": WORKLOAD_DESC[workload], "nodes": n, "yaw_bins": s.yaw_bins,
+        "config": {"workload": desc, "nodes": n, "yaw_bins": s.yaw_bins,
                    "rays_per_node_yaw": s.width * s.height, "max_depth": max_depth,
                    "inputs_sha256_16": synth.sha256(prob.map.grid, prob.tree.parent, prob.tree.pos)[:16],
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}",
+                   "count_pass": count_pass},
         "replans_per_s": ws * steps / (total_ms / 1e3),
         "nodes_per_s": ws * n * steps / (total_ms / 1e3),
         "replan_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -763,6 +775,10 @@ def main():
                     help="serving: arrival window (the workload specifies 30 s; at 20 Hz per robot the queue "
                          "grows by ~280 requests per second, so the default run replays the first 3 s)")
     ap.add_argument("--batch-repeats", type=int, default=3)
+    ap.add_argument("--count-pass", default="auto", choices=sorted(COUNT_PASSES),
+                    help="single-tree workloads: the counting kernels (default: the library's choice)")
+    ap.add_argument("--first-nodes", type=int, default=0,
+                    help="single-tree workloads: evaluate only the tree's first N nodes (a smaller case)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, _ = dist_env()
@@ -795,7 +811,8 @@ def main():
     else:
         workload = "large" if args.workload == "headline" else args.workload
         res = measure_single(workload, args.steps, args.warmup,
-                             with_modes=not args.no_modes and args.workload != "headline")
+                             with_modes=not args.no_modes and args.workload != "headline", count_pass=args.count_pass,
+                             first_nodes=args.first_nodes)
         if args.workload == "headline" and ws == 1 and not args.no_extras:
             res["paper_scale"] = summary(measure_single("paper_scale", args.steps, args.warmup))
             res["batched"] = batched_compare(repeats=args.batch_repeats)

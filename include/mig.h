@@ -320,7 +320,7 @@ typedef struct mig_kernel_times {
  * owns it (its centre's projection): MIG_COUNT_PAIRS enumerates each (node, yaw) frustum,
  * MIG_COUNT_NODES each node's voxels once for all yaws (at most 64 yaws; its ancestor test runs
  * once per voxel), MIG_COUNT_AUTO (the default) takes the per-node pass when a voxel lies in at least
- * 6 yaws' frusta on average. MIG_COUNT_RAYS walks every ray through every voxel it crosses and
+ * 3 yaws' frusta on average. MIG_COUNT_RAYS walks every ray through every voxel it crosses and
  * owner-tests the unknown ones. The owned-voxel kernels keep one uint16 step count per (node, yaw,
  * pixel) of a level in a buffer of at most steps_budget_bytes (0 = the default, 1 GiB); a level
  * that does not fit is counted in chunks. Errors: MIG_EINVAL (ctx NULL, unknown kernel). */

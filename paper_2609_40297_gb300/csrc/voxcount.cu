@@ -28,6 +28,12 @@ using namespace dev;
 
 constexpr int kCastWarps = 8;   // 256-thread CTAs, one ray per thread
 constexpr int kVoxWarps = 8;
+// The voxel passes hand out their work in groups of (node, yaw) pairs or nodes whose step counts
+// fit in this many bytes, so that the step counts the warps in flight read stay in L2.
+#ifndef MIG_STEPS_GROUP_BYTES
+#define MIG_STEPS_GROUP_BYTES (64u << 20)
+#endif
+constexpr size_t kStepsGroupBytes = MIG_STEPS_GROUP_BYTES;
 
 __device__ __forceinline__ int level_pairs(const LevelParams &p) {
     return (p.level_off[p.lvl + 1] - p.level_off[p.lvl]) * p.K;
@@ -130,14 +136,18 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) voxel_kernel(const LevelPar
     const size_t WH = (size_t)p.W * p.H;
     uint32_t st_cand = 0, st_unk = 0, st_visit = 0, st_anc = 0, st_reads = 0;
     int cur_node = -1, na = 0;
-    // items are handed out one at a time from the launch's counter: every pair's slice at the node's
-    // own height first, then outwards alternately above and below
+    // items are handed out one at a time from the launch's counter, in groups of pairs whose step
+    // counts stay in L2 together; within a group every pair's slice at the node's own height first,
+    // then outwards alternately above and below
+    const int grp = (int)max((size_t)1, min((size_t)npairs, kStepsGroupBytes / (WH * sizeof(uint16_t))));
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(p.vctr, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= items) break;
-        const int rank = it / npairs, ql = it % npairs;
+        const int g = it / (grp * slices), r = it - g * grp * slices;
+        const int gsz = min(grp, npairs - g * grp);
+        const int rank = r / gsz, ql = g * grp + r % gsz;
         const int zi = Rv + ((rank & 1) ? (rank + 1) >> 1 : -(rank >> 1));
         const int qq = p.q0 + ql;
         const int n = p.level_nodes[l0 + qq / p.K], k = qq % p.K;
@@ -370,12 +380,18 @@ __device__ __forceinline__ void anc_stage_node(const LevelParams &p, NodeQueues 
 // counters at the end of the item).
 constexpr int kNodeMaxK = 64;  // yaws of the per-node pass (one mask word, per-warp counters)
 
+// Blocks of 32 rows covering one slice's rows of the range ball (at most 2 Rv + 3 rows, Rv = T + 2
+// voxels): the per-node pass hands out (node, slice, row block) items.
+__host__ __device__ inline int node_row_blocks(int64_t Tq) { return (2 * ((int)(Tq >> 16) + 2) + 3 + 31) / 32; }
+
 // Per-warp state of the per-node pass: queues of unknown voxels in the band and of counted voxels
 // with the mask of the yaws that count them, and the per-yaw (absolute, marginal) counters.
 struct NodeWarp {
     unsigned long long unk[64];    // x | y << 12
     unsigned long long key[64];    // x | y << 12 | k_lo << 24 (first yaw of the mask)
     unsigned long long mask[64];   // yaws (from k_lo, cyclic) that count the voxel
+    unsigned long long vm[32];     // stage B: mask of the yaws counting each of the 32 voxels
+    unsigned long long xq[64];     // stage B: (voxel, yaw) pairs left to the exact visit test
     int cnt[2 * kNodeMaxK];
 };
 
@@ -440,22 +456,43 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
     const int Rv = (int)(p.Tq >> 16) + 2;
     const int slices = 2 * Rv + 1;
     const int nn = nb1 - nb0;
-    const int items = nn * slices;
+    const int yb_n = node_row_blocks(p.Tq);
+    const int items = nn * slices * yb_n;
     const float R = (float)p.Tq * (1.0f / 65536.0f) + 1.0f, R2 = R * R;
     const int gnx = p.grid.nx, gny = p.grid.ny, gnz = p.grid.nz;
     const size_t WH = (size_t)p.W * p.H;
     const float s16 = 1.0f / 65536.0f, yaw_scale = (float)K * 0.15915494309189535f;  // K / (2 pi)
+    const float Tv = (float)p.Tq * s16;  // the range in voxels
     uint32_t st_cand = 0, st_unk = 0, st_visit = 0, st_anc = 0, st_reads = 0, st_smp = 0;
     int cur_node = -1, na = 0;
-    // items are handed out one at a time from the launch's counter: every node's slice at its own
-    // height first (the fullest), then outwards alternately above and below
+    // the per-warp counters hold the counts of node cur_node until they are added to the level's
+    auto flush_counts = [&](int node) {
+        for (int t = lane; t < 2 * K; t += 32) {
+            const int v = Q.cnt[t];
+            if (v) {
+                atomicAdd(p.cnt + ((size_t)node * K + (t >> 1)) * 2 + (t & 1), v);
+                Q.cnt[t] = 0;
+            }
+        }
+        __syncwarp();
+    };
+    // items are handed out one at a time from the launch's counter, in groups of nodes whose step
+    // counts stay in L2 together; within a group every node's slice at its own height first (the
+    // fullest), then outwards alternately above and below, and within a slice the 32-row blocks from
+    // the middle outwards
+    const int per_node = slices * yb_n;
+    const int grp = (int)max((size_t)1, min((size_t)nn, kStepsGroupBytes / ((size_t)K * WH * sizeof(uint16_t))));
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(p.vctr, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= items) break;
-        const int rank = it / nn, ln = it % nn;
+        const int g = it / (grp * per_node), r = it - g * grp * per_node;
+        const int gsz = min(grp, nn - g * grp);
+        const int rzy = r / gsz, ln = g * grp + r % gsz;
+        const int rank = rzy / yb_n, rb = rzy - rank * yb_n;
         const int zi = Rv + ((rank & 1) ? (rank + 1) >> 1 : -(rank >> 1));
+        const int yblk = (yb_n - 1) / 2 + ((rb & 1) ? (rb + 1) >> 1 : -(rb >> 1));
         const int n = p.level_nodes[l0 + nb0 + ln];
         const int4 nd = p.node[n];
         const int v0x = nd.x >> 16, v0y = nd.y >> 16, v0z = nd.z >> 16;
@@ -474,7 +511,12 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
                 (rz < 0.f && p.band_tlo > -1e29f && rz < p.band_tlo * rho_max - eps))
                 continue;
         }
+        const float hy = sqrtf(h2);
+        const int ylo = max(0, (int)floorf(Pyf - hy) - 1), yhi = min(gny - 1, (int)ceilf(Pyf + hy) + 1);
+        const int yb = ylo + 32 * yblk;  // this item's rows: block yblk of the slice's rows [ylo, yhi]
+        if (yb > yhi) continue;
         if (n != cur_node) {  // the node's ancestors (Sec. IV-B), parent first
+            if (cur_node >= 0) flush_counts(cur_node);
             const int2 ar = p.anc_range[n];
             na = ar.y;
             if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
@@ -488,46 +530,87 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
         int nu = 0, nq = 0;
 
         // stage B: for 32 voxels (one per lane), the yaws that count them: every yaw whose frustum may
-        // hold the voxel (azimuth window) in turn
+        // hold the voxel (azimuth window) in turn gets its owner pixel (Eq. 5) and the reach test by
+        // step index; the visit test is decided by visit_surely where it can, else queued for the exact
+        // test, which runs 32 pairs at a time
         auto yaw_stage = [&](bool full) {
             const bool have = full || lane < nu;
             const unsigned long long e = full ? q_pop32(Q.unk, nu, lane) : Q.unk[lane];
             if (!full) nu = 0;
             const int x = (int)(e & 0xFFF), y = (int)((e >> 12) & 0xFFF);
-            const int rxq = (x << 16) + 32768 - nd.x, ryq = (y << 16) + 32768 - nd.y;
-            const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(y) - Pyf;
-            const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
             // the yaws whose frustum may hold the centre: psi_k within az_half of its azimuth (every
             // yaw near the vertical axis)
+            const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(y) - Pyf;
             int klo = 0, nk = have ? K : 0;
             if (have && fxr * fxr + fyr * fyr >= 4.0f && p.az_half < 3.0f) {
                 const float phi = atan2f(fyr, fxr);
-                const int a0 = (int)ceilf((phi - p.az_half) * yaw_scale), a1 = (int)floorf((phi + p.az_half) * yaw_scale);
+                const int a0 = (int)ceilf((phi - p.az_half) * yaw_scale);
+                const int a1 = (int)floorf((phi + p.az_half) * yaw_scale);
                 nk = max(0, min(K, a1 - a0 + 1));
                 klo = ((a0 % K) + K) % K;
             }
+            Q.vm[lane] = 0ull;
+            int nx = 0;  // (voxel, yaw) pairs queued in Q.xq for the exact visit test
+            // exact visit test by the owner ray (event order of its DDA, range) of 32 queued pairs; the
+            // pairs that pass set their bit in the voxel's mask word
+            auto exact_stage = [&](bool xfull) {
+                const bool xh = xfull || lane < nx;
+                const unsigned long long q = xfull ? q_pop32(Q.xq, nx, lane) : Q.xq[lane];
+                if (!xfull) nx = 0;
+                if (xh) {
+                    const int qx = (int)(q & 0xFFF), qy = (int)((q >> 12) & 0xFFF);
+                    const int pix = (int)((q >> 24) & 0x3FFFFF), k = (int)((q >> 46) & 0x3F);
+                    const int j = (int)((q >> 52) & 0x3F), r = (int)(q >> 58);
+                    int dx, dy, dz;
+                    ray_dir(p.body[pix], s_yi[12 * k], s_yi[12 * k + 1], dx, dy, dz);
+                    if (visit_index(nd.x, nd.y, nd.z, dx, dy, dz, qx, qy, z, p.Tq) >= 0) atomicOr(Q.vm + r, 1ull << j);
+                }
+                __syncwarp();
+            };
+            __syncwarp();
+            const int rxq = (x << 16) + 32768 - nd.x, ryq = (y << 16) + 32768 - nd.y;
+            const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
             unsigned long long mask = 0ull;
-            for (int j = 0; j < nk; ++j) {
-                int k = klo + j;
-                k -= k >= K ? K : 0;
-                const int *r = s_yi + 12 * k;
-                const float *f = s_yf + 9 * k;
-                const int64_t Z = (int64_t)r[8] * rxq + (int64_t)r[9] * ryq + (int64_t)r[10] * zq;
-                if (Z <= 0) continue;
-                const int64_t U = (int64_t)r[2] * rxq + (int64_t)r[3] * ryq + (int64_t)r[4] * zq;
-                const int64_t V = (int64_t)r[5] * rxq + (int64_t)r[6] * ryq + (int64_t)r[7] * zq;
-                const float zi_ = __fdividef(1.0f, fmaf(f[6], fxr, fmaf(f[7], fyr, f[8] * rz)));
-                int pu, pv;
-                if (!pixel_in(U, Z, fmaf(f[0], fxr, fmaf(f[1], fyr, f[2] * rz)) * zi_, p.W, pu)) continue;
-                if (!pixel_in(V, Z, fmaf(f[3], fxr, fmaf(f[4], fyr, f[5] * rz)) * zi_, p.H, pv)) continue;
-                const int pix = pv * p.W + pu;
-                if (man >= (int)__ldg(steps + (size_t)k * WH + pix)) continue;  // behind the owner ray's hit
-                if constexpr (STATS) ++st_visit;
-                int dx, dy, dz;
-                ray_dir(p.body[pix], r[0], r[1], dx, dy, dz);
-                if (visit_index(nd.x, nd.y, nd.z, dx, dy, dz, x, y, z, p.Tq) >= 0) mask |= 1ull << j;
+            const int nk_max = __reduce_max_sync(0xffffffffu, (unsigned)nk);
+            for (int j = 0; j < nk_max; ++j) {
+                bool exact = false;
+                int pix = 0, k = 0;
+                if (j < nk) {
+                    k = klo + j;
+                    k -= k >= K ? K : 0;
+                    const int *rw = s_yi + 12 * k;
+                    const float *fw = s_yf + 9 * k;
+                    const int64_t Z = (int64_t)rw[8] * rxq + (int64_t)rw[9] * ryq + (int64_t)rw[10] * zq;
+                    if (Z > 0) {
+                        const int64_t U = (int64_t)rw[2] * rxq + (int64_t)rw[3] * ryq + (int64_t)rw[4] * zq;
+                        const int64_t V = (int64_t)rw[5] * rxq + (int64_t)rw[6] * ryq + (int64_t)rw[7] * zq;
+                        const float zi_ = __fdividef(1.0f, fmaf(fw[6], fxr, fmaf(fw[7], fyr, fw[8] * rz)));
+                        int pu, pv;
+                        if (pixel_in(U, Z, fmaf(fw[0], fxr, fmaf(fw[1], fyr, fw[2] * rz)) * zi_, p.W, pu) &&
+                            pixel_in(V, Z, fmaf(fw[3], fxr, fmaf(fw[4], fyr, fw[5] * rz)) * zi_, p.H, pv)) {
+                            pix = pv * p.W + pu;
+                            if (man < (int)__ldg(steps + (size_t)k * WH + pix)) {  // before the owner ray's hit
+                                if constexpr (STATS) ++st_visit;
+                                int dx, dy, dz;
+                                ray_dir(p.body[pix], rw[0], rw[1], dx, dy, dz);
+                                if (visit_surely(fxr, fyr, rz, dx, dy, dz, Tv)) mask |= 1ull << j;
+                                else exact = true;
+                            }
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, exact);
+                if (exact)
+                    Q.xq[nx + __popc(bal & lt_mask)] = (unsigned long long)x | ((unsigned long long)y << 12) |
+                                                       ((unsigned long long)pix << 24) | ((unsigned long long)k << 46) |
+                                                       ((unsigned long long)j << 52) | ((unsigned long long)lane << 58);
+                nx += __popc(bal);
+                __syncwarp();
+                if (nx >= 32) exact_stage(true);
             }
-            const bool put = mask != 0ull;
+            if (nx > 0) exact_stage(false);
+            mask |= Q.vm[lane];
+            const bool put = have && mask != 0ull;
             const unsigned bal = __ballot_sync(0xffffffffu, put);
             if (put) {
                 const int slot = nq + __popc(bal & lt_mask);
@@ -539,9 +622,7 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
             if (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
         };
 
-        const float hy = sqrtf(h2);
-        const int ylo = max(0, (int)floorf(Pyf - hy) - 1), yhi = min(gny - 1, (int)ceilf(Pyf + hy) + 1);
-        for (int yb = ylo; yb <= yhi; yb += 32) {
+        {
             const int y = yb + lane;
             int xa = 0, len = 0;
             if (y <= yhi) {
@@ -594,16 +675,8 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
         if (nu > 0) yaw_stage(false);
         while (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
         if (nq > 0) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, false);
-        // this slice's counts into the level's counters
-        for (int t = lane; t < 2 * K; t += 32) {
-            const int v = Q.cnt[t];
-            if (v) {
-                atomicAdd(p.cnt + ((size_t)n * K + (t >> 1)) * 2 + (t & 1), v);
-                Q.cnt[t] = 0;
-            }
-        }
-        __syncwarp();
     }
+    if (cur_node >= 0) flush_counts(cur_node);
     if constexpr (STATS) {
         st_cand = __reduce_add_sync(0xffffffffu, st_cand);
         st_unk = __reduce_add_sync(0xffffffffu, st_unk);
@@ -707,16 +780,17 @@ int node_ctas_per_sm() {
 }
 
 // The per-node pass, when it applies: whole nodes in a chunk, at most kNodeMaxK yaws and a frustum
-// band. By default it is taken when a voxel lies in at least 6 yaws' frusta on average (K times the
-// azimuth half-width over pi): below that the per-pair pass runs faster.
+// band. By default it is taken when a voxel lies in at least 3 yaws' frusta on average (K times the
+// azimuth half-width over pi; 4 at paper scale, 9 on the large workload, where it runs 1.2x and 1.3x
+// faster than the per-pair pass).
 bool node_pass(const LevelParams &p) {
     if (!(p.az_half > 0.f && p.K <= kNodeMaxK && p.steps_cap >= p.K) || p.voxel_pass == MIG_COUNT_PAIRS) return false;
-    return p.voxel_pass == MIG_COUNT_NODES || (float)p.K * p.az_half >= 6.0f * 3.14159265f;
+    return p.voxel_pass == MIG_COUNT_NODES || (float)p.K * p.az_half >= 3.0f * 3.14159265f;
 }
 
 void launch_node_chunk(const LevelParams &c, int num_sms, int node_ctas, cudaStream_t s) {
     const int slices = 2 * ((int)(c.Tq >> 16) + 2) + 1;
-    const long long items = (long long)((c.q1 - c.q0) / c.K) * slices;
+    const long long items = (long long)((c.q1 - c.q0) / c.K) * slices * node_row_blocks(c.Tq);
     const int g = (int)std::max<long long>(1, std::min<long long>((items + kVoxWarps - 1) / kVoxWarps,
                                                                    (long long)num_sms * node_ctas));
     const size_t smem = node_dyn_smem(c.max_anc);
@@ -724,7 +798,17 @@ void launch_node_chunk(const LevelParams &c, int num_sms, int node_ctas, cudaStr
     else node_kernel<false><<<g, kVoxWarps * 32, smem, s>>>(c);
 }
 
-int vox_chunk_pairs(const LevelParams &p) { return node_pass(p) ? (p.steps_cap / p.K) * p.K : p.steps_cap; }
+// Pairs per launch: within the step-count buffer, and few enough that the launch's work items
+// (pairs x slices, or nodes x slices x row blocks) stay below 2^30 for the 32-bit work counter.
+int vox_chunk_pairs(const LevelParams &p) {
+    const long long slices = 2 * ((long long)(p.Tq >> 16) + 2) + 1;
+    const long long lim = 1ll << 30;
+    if (node_pass(p)) {
+        const long long nodes = std::min<long long>(p.steps_cap / p.K, lim / (slices * node_row_blocks(p.Tq)));
+        return (int)std::max<long long>(1, nodes) * p.K;
+    }
+    return (int)std::max<long long>(1, std::min<long long>(p.steps_cap, lim / slices));
+}
 
 void launch_vox_level(const LevelParams &p, long long pairs, int num_sms, int vox_ctas, int node_ctas, cudaStream_t s) {
     const int cap = vox_chunk_pairs(p);

@@ -208,8 +208,9 @@ size_t map_layout_bytes(int nx, int ny, int nz, int *nbx, int *nby, int *nbz) {
     *nby = (ny + 7) / 8;
     *nbz = (nz + 7) / 8;
 #if MIG_LAYOUT == 1
-    // voxel codes, then (256-byte aligned) one occupancy byte per 8x8x8 brick
-    return bocc_offset(nx, ny, nz) + (size_t)*nbx * *nby * *nbz;
+    // voxel codes, then (256-byte aligned) one occupancy byte per 8x8x8 brick and (256-byte aligned)
+    // one per 32x32x32 super-brick
+    return occ_summary_end(nx, ny, nz);
 #else
     return (size_t)*nbx * *nby * *nbz * 512;
 #endif

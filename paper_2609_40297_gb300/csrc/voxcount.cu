@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
     const long long items = (long long)(q1 - p.q0) * tx * ty;
     const size_t WH = (size_t)p.W * p.H;
     const uint8_t *bocc = p.grid.g + bocc_offset(p.grid.nx, p.grid.ny, p.grid.nz);
+    const uint8_t *sbocc = p.grid.g + sbocc_offset(p.grid.nx, p.grid.ny, p.grid.nz);
     uint32_t st_rays = 0, st_fine = 0, st_skip = 0;
     for (long long it = (long long)blockIdx.x * kCastWarps + (threadIdx.x >> 5); it < items;
          it += (long long)gridDim.x * kCastWarps) {
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
         const int32_t *yk = p.yawtab + k * 12;
         int dx, dy, dz;
         ray_dir(b, yk[0], yk[1], dx, dy, dz);
-        const uint32_t m = cast_hit<STATS>(p.grid.g, bocc, p.grid.nx, p.grid.ny, p.grid.nz, nd.x, nd.y, nd.z, dx, dy,
+        const uint32_t m = cast_hit<STATS>(p.grid.g, bocc, sbocc, p.grid.nx, p.grid.ny, p.grid.nz, nd.x, nd.y, nd.z, dx, dy,
                                            dz, p.Tq, st_fine, st_skip);
         p.steps[(size_t)ql * WH + (size_t)j * p.W + i] = (uint16_t)m;
         if constexpr (STATS) ++st_rays;
@@ -720,6 +721,26 @@ __global__ void bocc_kernel(uint8_t *grid, int nx, int ny, int nz, int bx0, int 
     }
 }
 
+// Recomputes the occupancy byte of every super-brick in [s0, s1) (super-brick coordinates) from its
+// bricks' bytes.
+__global__ void sbocc_kernel(uint8_t *grid, int nx, int ny, int nz, int sx0, int sy0, int sz0, int sx1, int sy1,
+                             int sz1) {
+    const int nbx = (nx + 7) >> 3, nby = (ny + 7) >> 3, nbz = (nz + 7) >> 3;
+    const int nsx = (nx + 31) >> 5, nsy = (ny + 31) >> 5;
+    const uint8_t *bocc = grid + bocc_offset(nx, ny, nz);
+    uint8_t *sbocc = grid + sbocc_offset(nx, ny, nz);
+    const int wx = sx1 - sx0, wy = sy1 - sy0;
+    const long long total = (long long)wx * wy * (sz1 - sz0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int sx = sx0 + (int)(i % wx), sy = sy0 + (int)((i / wx) % wy), sz = sz0 + (int)(i / ((long long)wx * wy));
+        uint8_t occ = 0;
+        for (int bz = 4 * sz; bz < min(4 * sz + 4, nbz); ++bz)
+            for (int by = 4 * sy; by < min(4 * sy + 4, nby); ++by)
+                for (int bx = 4 * sx; bx < min(4 * sx + 4, nbx); ++bx) occ |= bocc[((size_t)bz * nby + by) * nbx + bx];
+        sbocc[((size_t)sz * nsy + sy) * nsx + sx] = occ ? 1 : 0;
+    }
+}
+
 }  // namespace
 
 size_t vox_dyn_smem(int max_anc) { return (size_t)kVoxWarps * (size_t)std::max(1, max_anc) * sizeof(AncRec); }
@@ -828,6 +849,12 @@ void launch_bocc(uint8_t *grid, int nx, int ny, int nz, int x0, int y0, int z0, 
     const long long total = (long long)(bx1 - bx0) * (by1 - by0) * (bz1 - bz0);
     const int grid_ = (int)std::max<long long>(1, std::min<long long>((total + 7) / 8, 4096));
     bocc_kernel<<<grid_, 256, 0, s>>>(grid, nx, ny, nz, bx0, by0, bz0, bx1, by1, bz1);
+    // the super-bricks holding those bricks
+    const int sx0 = bx0 >> 2, sy0 = by0 >> 2, sz0 = bz0 >> 2;
+    const int sx1 = (bx1 + 3) >> 2, sy1 = (by1 + 3) >> 2, sz1 = (bz1 + 3) >> 2;
+    const long long stotal = (long long)(sx1 - sx0) * (sy1 - sy0) * (sz1 - sz0);
+    const int sgrid = (int)std::max<long long>(1, std::min<long long>((stotal + 255) / 256, 1024));
+    sbocc_kernel<<<sgrid, 256, 0, s>>>(grid, nx, ny, nz, sx0, sy0, sz0, sx1, sy1, sz1);
 }
 
 }  // namespace mig

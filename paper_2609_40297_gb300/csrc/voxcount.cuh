@@ -32,12 +32,22 @@ MIG_HD uint8_t ld_u8(const uint8_t *p) {
 #endif
 }
 
-// Brick occupancy summary of a map: one byte per 8x8x8 brick (x-fastest), 1 iff the brick holds
-// an occupied voxel. It sits after the voxel codes in the map's allocation (at a 256-byte aligned
-// offset), so that every copy of a grid carries its summary.
+// Occupancy summaries of a map: one byte per 8x8x8 brick (x-fastest), 1 iff the brick holds an
+// occupied voxel, then one byte per 32x32x32 super-brick (4x4x4 bricks), 1 iff one of its bricks
+// does. They sit after the voxel codes in the map's allocation (each at a 256-byte aligned offset),
+// so that every copy of a grid carries its summaries.
 constexpr int kOccBrickShift = 3;
+constexpr int kOccSuperShift = 5;
 MIG_HD size_t bocc_offset(int nx, int ny, int nz) {
     return ((size_t)nx * ny * nz + 255) & ~(size_t)255;
+}
+MIG_HD size_t sbocc_offset(int nx, int ny, int nz) {
+    const size_t nb = (size_t)((nx + 7) >> 3) * (size_t)((ny + 7) >> 3) * (size_t)((nz + 7) >> 3);
+    return bocc_offset(nx, ny, nz) + ((nb + 255) & ~(size_t)255);
+}
+MIG_HD size_t occ_summary_end(int nx, int ny, int nz) {
+    return sbocc_offset(nx, ny, nz) +
+           (size_t)((nx + 31) >> 5) * (size_t)((ny + 31) >> 5) * (size_t)((nz + 31) >> 5);
 }
 
 // Event order: (t1, axis1) < (t2, axis2) with t = n / ad, compared exactly by cross products.
@@ -95,11 +105,14 @@ MIG_HD int ev_argmin3(uint32_t n0, uint32_t a0, uint32_t n1, uint32_t a1, uint32
     return bz ? 2 : (xly ? 0 : 1);
 }
 
-// Crossing index (from the start, 0-based) of the crossing that leaves the 8-voxel brick of voxel v
-// along an axis with step s: the brick's last voxel in the direction of travel, or the grid's.
-MIG_HD int brick_exit_crossing(int v, int v0, int s, int N) {
-    return s > 0 ? min(v | 7, N - 1) - v0 : v0 - (v & ~7);
+// Crossing index (from the start, 0-based) of the crossing that leaves the cell of 2^shift voxels
+// (a brick or a super-brick) of voxel v along an axis with step s: the cell's last voxel in the
+// direction of travel, or the grid's.
+MIG_HD int cell_exit_crossing(int v, int v0, int s, int N, int shift) {
+    const int m = (1 << shift) - 1;
+    return s > 0 ? min(v | m, N - 1) - v0 : v0 - (v & ~m);
 }
+MIG_HD int brick_exit_crossing(int v, int v0, int s, int N) { return cell_exit_crossing(v, v0, s, N, kOccBrickShift); }
 
 // Crossings an axis may take: those that stay inside the grid and start before the range T (the
 // k-th crossing, k = 0, 1, ..., is at face distance n0 + k 2^16, i.e. at t = (n0 + k 2^16) / ad).
@@ -115,14 +128,17 @@ MIG_HD int allowed_crossings(int v0, int s, uint32_t n0, uint32_t ad, int N, int
 // stops on that voxel and visits no voxel beyond it. A voxel is visited iff its entering crossing
 // is allowed (inside the grid, before the range T); per axis the allowed crossings are a prefix
 // of its crossings, so each step compares one crossing index (or face distance) with a limit
-// fixed at the start. Bricks without an occupied voxel are crossed by a brick-level walk whose
-// crossings are exactly the brick faces of the voxel walk, in the same order; on entering a brick
-// with an occupied voxel the voxel state there is rebuilt exactly from the start (per axis, the
-// crossings that precede the entering event) and the voxel walk continues. `fine` and `coarse`
-// count voxel and brick steps (statistics).
+// fixed at the start. Cells without an occupied voxel are crossed by a cell-level walk whose
+// crossings are exactly the cell faces of the voxel walk, in the same order: super-bricks
+// (32 voxels a side) where `sbocc` marks them free, else bricks (8 a side) where `bocc` does. On
+// entering a cell that holds an occupied voxel (or, from the brick walk, a free super-brick) the
+// voxel state there is rebuilt exactly from the start (per axis, the crossings that precede the
+// entering event) and the walk continues at the finer (or coarser) level. Null summaries disable
+// their level. `fine` and `coarse` count voxel and cell steps (statistics).
 template <bool STATS>
-MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, int gnx, int gny, int gnz, int Px, int Py, int Pz,
-                         int dx, int dy, int dz, int64_t Tq, uint32_t &fine, uint32_t &coarse) {
+MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, const uint8_t *sbocc, int gnx, int gny, int gnz,
+                         int Px, int Py, int Pz, int dx, int dy, int dz, int64_t Tq, uint32_t &fine,
+                         uint32_t &coarse) {
     int v0x, v0y, v0z, sx, sy, sz;
     uint32_t n0x, n0y, n0z, ax, ay, az;
     ray_axis(Px, dx, v0x, sx, n0x, ax);
@@ -133,11 +149,61 @@ MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, int gnx, int gny
     // face limits: a crossing at face distance n along an axis is allowed iff n < l
     const uint32_t lx = n0x + ((uint32_t)kx << 16), ly = n0y + ((uint32_t)ky << 16), lz = n0z + ((uint32_t)kz << 16);
     const int nbx = (gnx + 7) >> 3, nby = (gny + 7) >> 3;
+    const int nsx = (gnx + 31) >> 5, nsy = (gny + 31) >> 5;
     const int dax = sx, day = sy * gnx, daz = sz * gnx * gny;
     // voxel state (valid in the voxel walk): current voxel, next crossing per axis, step index
     int vx = v0x, vy = v0y, vz = v0z;
     uint32_t nx = n0x, ny = n0y, nz = n0z, m = 0;
+    // the voxel state after the event (NE / AE, e) that enters along e by crossing Ee, from the start;
+    // ex, ey, ez: crossings of the other axes that come after that event
+    auto enter = [&](uint32_t NE, uint32_t AE, int e, int Ee, int ex, int ey, int ez) {
+        const float tE = fast_div(NE, AE);
+        const int cx = e == 0 ? Ee + 1 : crossings_before(n0x, ax, 0, ex, NE, AE, e, tE);
+        const int cy = e == 1 ? Ee + 1 : crossings_before(n0y, ay, 1, ey, NE, AE, e, tE);
+        const int cz = e == 2 ? Ee + 1 : crossings_before(n0z, az, 2, ez, NE, AE, e, tE);
+        vx = v0x + sx * cx;
+        vy = v0y + sy * cy;
+        vz = v0z + sz * cz;
+        nx = n0x + ((uint32_t)cx << 16);
+        ny = n0y + ((uint32_t)cy << 16);
+        nz = n0z + ((uint32_t)cz << 16);
+        m = (uint32_t)(cx + cy + cz);
+    };
+    int occ_super = -1;  // the super-brick last found to hold an occupied voxel (not read again)
     for (;;) {
+        const int si = ((vz >> 5) * nsy + (vy >> 5)) * nsx + (vx >> 5);
+        if (sbocc && si != occ_super && !ld_u8(sbocc + si)) {
+            // super-brick walk: per axis the crossing index (from the start) that leaves the current
+            // super-brick, until the ray enters one that holds an occupied voxel
+            int ex = cell_exit_crossing(vx, v0x, sx, gnx, kOccSuperShift), ey = cell_exit_crossing(vy, v0y, sy, gny, kOccSuperShift),
+                ez = cell_exit_crossing(vz, v0z, sz, gnz, kOccSuperShift);
+            int bx = vx >> 5, by = vy >> 5, bz = vz >> 5;
+            for (;;) {
+                if constexpr (STATS) ++coarse;
+                const uint32_t Nx = n0x + ((uint32_t)ex << 16), Ny = n0y + ((uint32_t)ey << 16), Nz = n0z + ((uint32_t)ez << 16);
+                const int e = ev_argmin3(Nx, ax, Ny, ay, Nz, az);
+                const int Ee = e == 0 ? ex : (e == 1 ? ey : ez);
+                if (Ee >= (e == 0 ? kx : (e == 1 ? ky : kz))) return kNoHit;  // leaves the grid or the range
+                const uint32_t NE = e == 0 ? Nx : (e == 1 ? Ny : Nz), AE = e == 0 ? ax : (e == 1 ? ay : az);
+                const int s_e = e == 0 ? sx : (e == 1 ? sy : sz), v0e = e == 0 ? v0x : (e == 1 ? v0y : v0z);
+                const int ue = v0e + s_e * (Ee + 1);
+                const int nEe = cell_exit_crossing(ue, v0e, s_e, e == 0 ? gnx : (e == 1 ? gny : gnz), kOccSuperShift);
+                bx = e == 0 ? ue >> 5 : bx;
+                by = e == 1 ? ue >> 5 : by;
+                bz = e == 2 ? ue >> 5 : bz;
+                const int ox = ex, oy = ey, oz = ez;
+                ex = e == 0 ? nEe : ex;
+                ey = e == 1 ? nEe : ey;
+                ez = e == 2 ? nEe : ez;
+                if (ld_u8(sbocc + (bz * nsy + by) * nsx + bx)) {
+                    enter(NE, AE, e, Ee, ox, oy, oz);
+                    occ_super = (bz * nsy + by) * nsx + bx;
+                    break;
+                }
+            }
+            continue;
+        }
+        occ_super = si;
         if (!bocc || ld_u8(bocc + ((vz >> 3) * nby + (vy >> 3)) * nbx + (vx >> 3))) {
             // voxel walk inside a brick that holds an occupied voxel, up to its faces: bnx.. = face
             // distance of the crossing that leaves the brick along each axis
@@ -164,7 +230,8 @@ MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, int gnx, int gny
             }
             continue;
         }
-        // brick walk: per axis the crossing index (from the start) that leaves the current brick
+        // brick walk: per axis the crossing index (from the start) that leaves the current brick,
+        // until the ray enters a brick that holds an occupied voxel or a super-brick that holds none
         int ex = brick_exit_crossing(vx, v0x, sx, gnx), ey = brick_exit_crossing(vy, v0y, sy, gny),
             ez = brick_exit_crossing(vz, v0z, sz, gnz);
         int bx = vx >> 3, by = vy >> 3, bz = vz >> 3;
@@ -180,26 +247,17 @@ MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, int gnx, int gny
             const int ue = v0e + s_e * (Ee + 1);
             const int nb = ue >> 3;
             const int nEe = brick_exit_crossing(ue, v0e, s_e, e == 0 ? gnx : (e == 1 ? gny : gnz));
+            const bool new_super = (nb >> 2) != ((e == 0 ? bx : (e == 1 ? by : bz)) >> 2);
             bx = e == 0 ? nb : bx;
             by = e == 1 ? nb : by;
             bz = e == 2 ? nb : bz;
+            const int ox = ex, oy = ey, oz = ez;
             ex = e == 0 ? nEe : ex;
             ey = e == 1 ? nEe : ey;
             ez = e == 2 ? nEe : ez;
-            if (ld_u8(bocc + (bz * nby + by) * nbx + bx)) {
-                // enter it: the voxel state after the entering event (NE, AE, e), from the start; the
-                // other axes' next brick faces (ex, ey, ez) come after that event
-                const float tE = fast_div(NE, AE);
-                const int cx = e == 0 ? Ee + 1 : crossings_before(n0x, ax, 0, ex, NE, AE, e, tE);
-                const int cy = e == 1 ? Ee + 1 : crossings_before(n0y, ay, 1, ey, NE, AE, e, tE);
-                const int cz = e == 2 ? Ee + 1 : crossings_before(n0z, az, 2, ez, NE, AE, e, tE);
-                vx = v0x + sx * cx;
-                vy = v0y + sy * cy;
-                vz = v0z + sz * cz;
-                nx = n0x + ((uint32_t)cx << 16);
-                ny = n0y + ((uint32_t)cy << 16);
-                nz = n0z + ((uint32_t)cz << 16);
-                m = (uint32_t)(cx + cy + cz);
+            if (ld_u8(bocc + (bz * nby + by) * nbx + bx) ||
+                (sbocc && new_super && !ld_u8(sbocc + ((bz >> 2) * nsy + (by >> 2)) * nsx + (bx >> 2)))) {
+                enter(NE, AE, e, Ee, ox, oy, oz);
                 break;
             }
         }

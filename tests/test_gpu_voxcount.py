@@ -150,6 +150,37 @@ def test_map_updates_refresh_brick_occupancy(ctx):
         m.close()
 
 
+def test_super_brick_walk_and_updates(ctx):
+    """A sparse map spanning several 32-voxel super-bricks (long rays cross free super-bricks in one
+    step each): single occupied voxels written into free super-bricks and cleared again by updates
+    change the results exactly as the oracle says."""
+    ctx.set_count_kernel(mig.COUNT_AUTO, 0)
+    rng = np.random.default_rng(17)
+    p = synth.random_small(23, nx=136, ny=100, nz=70, v=0.1, p_occ=0.00002, p_free=0.5, n_nodes=14, max_depth=4,
+                           sensor=Sensor(100, 70, 26, 18, 5.5, 6, 5.0))
+    g = p.map.grid.copy()
+    m = mig.Map(ctx, g, p.map.voxel_size, p.map.origin)
+    try:
+        _same(mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, want_counts=True, want_depth=True), _oracle(p, grid=g),
+              what="initial")
+        c = (np.asarray(p.tree.pos[0]) / p.map.voxel_size).astype(int)
+        spots = []
+        for it in range(4):
+            # an occupied voxel 20-50 voxels from the root, where the rays are sparse
+            off = rng.integers(20, 50, 3) * rng.choice([-1, 1], 3)
+            x, y, z = (int(np.clip(c[a] + off[a], 0, g.shape[2 - a] - 1)) for a in range(3))
+            box = np.full((1, 1, 1), 2, np.uint8)
+            if it == 3:  # clear the first one again
+                (x, y, z), box = spots[0], np.full((1, 1, 1), 1, np.uint8)
+            spots.append((x, y, z))
+            m.update(x, y, z, box)
+            g[z, y, x] = box[0, 0, 0]
+            got = mig.tree_eval(m, p.tree.parent, p.tree.pos, p.sensor, want_counts=True, want_depth=True)
+            _same(got, _oracle(p, grid=g), what=f"update {it} at {(x, y, z)}")
+    finally:
+        m.close()
+
+
 def test_stats_agree_between_kernels(ctx):
     """The instrumented pass re-runs the ray-by-ray kernel beside the owned-voxel one: both count the
     same samples, and the cast covers every ray."""

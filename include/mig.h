@@ -201,8 +201,8 @@ mig_status mig_tree_score_device(mig_ctx *ctx, int n, const int32_t *parent, con
  * A tree needs about n * width * height * 4 bytes plus n * (K * 8 + 64 + 4 * max_depth) bytes;
  * a larger request returns MIG_EINVAL with the size in mig_last_error. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) and keeps it for the life
- * of the process; make that first call before any stream capture, and do not call
- * cudaDeviceReset on that device afterwards (the array may move). Every call shares the one
+ * of the process; do not call cudaDeviceReset on that device afterwards (the array may move).
+ * The yaw table travels in kernel parameters, not by a copy from host memory. Every call shares the one
  * array: calls whose work overlaps on the GPU (other streams, other contexts on the same
  * device) race and corrupt each other. It counts with the ray-by-ray kernel (identical results).
  * --------------------------------------------------------------------------------------- */
@@ -236,7 +236,8 @@ mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_tree_desc *t
 typedef struct mig_tile_config {
     int32_t tile_w, tile_h;   /* count pass: pixel rays per warp work item (a multiple of 32, <= 4096) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM */
-    int32_t engine;           /* batches: 0 = one persistent dataflow kernel, 1 = per-tree launch
+    int32_t engine;           /* batches: 0 = one persistent dataflow kernel (the sample modes with at
+                                 most 64 yaws; other batches use engine 1), 1 = per-tree launch
                                  chains on concurrent streams in one graph */
 } mig_tile_config;
 mig_status mig_batch_set_tiles(mig_ctx *ctx, const mig_tile_config *cfg);
@@ -256,12 +257,13 @@ mig_status mig_batch_set_timeout(mig_ctx *ctx, int64_t timeout_us, int debug_sta
  * shape as the previous one replays the captured graph; the legacy default stream and
  * profiling use plain launches). */
 mig_status mig_batch_graph_stats(mig_ctx *ctx, uint64_t *captures, uint64_t *replays);
-/* Device-side trace of batched launches: with tracing on, every segment (the count or the render
- * work of one tree level) records when it became ready and when its last item finished
- * (microseconds from the kernel start, %globaltimer). mig_batch_trace_read copies the records of
- * the last traced launch (n = number available). Traced launches do not use the graph. */
+/* Device-side trace of batched launches: with tracing on, every segment (the cast or the voxel count
+ * of one chunk of a tree level's nodes, or the level's render work) records when it became ready and
+ * when its last item finished (microseconds from the kernel start, %globaltimer).
+ * mig_batch_trace_read copies the records of the last traced launch (n = number available).
+ * Traced launches do not use the graph. */
 typedef struct mig_trace_rec {
-    int32_t tree, level, phase, items; /* phase 0 = count, 1 = render */
+    int32_t tree, level, phase, items; /* phase 0 = cast, 1 = voxel count, 2 = render */
     double activated_us, done_us;
 } mig_trace_rec;
 mig_status mig_batch_trace(mig_ctx *ctx, int enable);

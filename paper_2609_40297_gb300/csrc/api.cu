@@ -94,7 +94,10 @@ mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out) {
     auto cam = std::make_unique<Camera>();
     mig_status st = camera_build(s, *cam);
     if (st != MIG_OK) return st;
-    const size_t bb = cam->body.size() * 4, yb = cam->yaw.size() * 4;
+    cam->yawf.resize((size_t)cam->K * 9);
+    for (int k = 0; k < cam->K; ++k)
+        for (int t = 0; t < 9; ++t) cam->yawf[(size_t)k * 9 + t] = (float)cam->yaw[(size_t)k * kYawRec + 2 + t] * (1.0f / 65536.0f);
+    const size_t bb = cam->body.size() * 4, yb = (cam->yaw.size() + cam->yawf.size()) * 4;
     cam->d_body = (int32_t *)ctx->alloc.alloc(bb, ctx->stream);
     cam->d_yaw = (int32_t *)ctx->alloc.alloc(yb, ctx->stream);
     if (!cam->d_body || !cam->d_yaw) {
@@ -103,7 +106,10 @@ mig_status ctx_camera(mig_ctx *ctx, const mig_sensor &s, const Camera **out) {
         return fail(MIG_ENOMEM, "camera table allocation failed");
     }
     MIG_CUDA_TRY(cudaMemcpyAsync(cam->d_body, cam->body.data(), bb, cudaMemcpyHostToDevice, ctx->stream));
-    MIG_CUDA_TRY(cudaMemcpyAsync(cam->d_yaw, cam->yaw.data(), yb, cudaMemcpyHostToDevice, ctx->stream));
+    cam->d_yawf = reinterpret_cast<const float *>(cam->d_yaw + cam->yaw.size());
+    MIG_CUDA_TRY(cudaMemcpyAsync(cam->d_yaw, cam->yaw.data(), cam->yaw.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    MIG_CUDA_TRY(cudaMemcpyAsync(const_cast<float *>(cam->d_yawf), cam->yawf.data(), cam->yawf.size() * 4,
+                                 cudaMemcpyHostToDevice, ctx->stream));
     MIG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // host tables may move with the vector
     *out = cam.get();
     ctx->cameras.push_back(std::move(cam));
@@ -261,6 +267,7 @@ static LevelParams level_params(const mig_map *m, const Camera *cam, const mig_c
     p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
     p.body = (const int4 *)cam->d_body;
     p.yawtab = cam->d_yaw;
+    p.yawf = cam->d_yawf;
     p.W = cam->W;
     p.H = cam->H;
     p.K = cam->K;
@@ -329,7 +336,7 @@ void mig_ctx_destroy(mig_ctx *ctx) {
     mig_batch_release(ctx);
     for (auto &c : ctx->cameras) {
         ctx->alloc.free(c->d_body, c->body.size() * 4, ctx->stream);
-        ctx->alloc.free(c->d_yaw, c->yaw.size() * 4, ctx->stream);
+        ctx->alloc.free(c->d_yaw, (c->yaw.size() + c->yawf.size()) * 4, ctx->stream);
         ctx->alloc.free(c->d_pano_bc, c->pano_bc.size() * 4, ctx->stream);
         ctx->alloc.free(c->d_pano_dir, c->pano_dir.size() * 4, ctx->stream);
         ctx->alloc.free(c->d_pano_row, c->pano_row.size() * 4, ctx->stream);

@@ -1,11 +1,11 @@
 // Batched evaluation of many independent trees in one persistent launch (Sec. IV-C per tree).
 //
-// Work items are ordered level-major over all trees: for level d, the count items (node, yaw,
-// tile) of every tree that has a level d, then the render items (internal node, 32 pixels) of
-// those trees. Warps take items from one atomic counter. A count item of tree t at level d
-// waits until level d-1 of tree t is complete (its depth buffers are written); the warp that
-// finishes the last count item of (t, d) performs the yaw selection of the level; a render item
-// waits for that selection. Every wait is bounded by a time limit; a wait that runs out sets an
+// Each tree level is a chain of segments (batch.h): per chunk of whole nodes a cast segment and a
+// per-node voxel segment (the owned-voxel count, voxitems.cuh), then a render segment. Warps take
+// item numbers from one atomic counter; a segment's items are numbered only once it is ready (its
+// predecessor complete), so warps only ever receive ready work. The warp that finishes a segment's
+// last item activates its successor; the one that finishes a level's last voxel segment first
+// selects the level's yaws. Every wait is bounded by a time limit; a wait that runs out sets an
 // abort flag, all warps leave, and the host returns MIG_ETIMEOUT.
 //
 // The host packs the plans of all trees into one upload, launches the persistent kernel and
@@ -21,9 +21,10 @@
 #include <memory>
 
 #include "batch.h"
-#include "voxcount.h"
 #include "dev_path.cuh"
 #include "kernels.h"
+#include "voxcount.h"
+#include "voxitems.cuh"
 
 namespace mig {
 namespace {
@@ -62,13 +63,6 @@ __device__ void activate(const BatchParams &bp, int seg) {
     store_release(bp.log_valid + pos, 1);
 }
 
-// Level (tree, level) is complete: its depth buffers are written; its next level becomes ready.
-__device__ void level_done(const BatchParams &bp, const BatchTree &T, int tree, int level) {
-    const int next = level + 1;
-    if (next < T.n_levels && bp.segs[2 * (T.lvl_base + next)].items > 0) activate(bp, 2 * (T.lvl_base + next));
-    (void)tree;
-}
-
 __device__ __forceinline__ bool timed_out(const BatchParams &bp, unsigned long long &deadline) {
     if (deadline == 0) deadline = global_ns() + bp.timeout_ns;
     if (global_ns() > deadline) {
@@ -79,18 +73,31 @@ __device__ __forceinline__ bool timed_out(const BatchParams &bp, unsigned long l
     return false;
 }
 
+constexpr int kBatchWarps = 8;
+
 #ifndef MIG_BATCH_MINB
-#define MIG_BATCH_MINB MIG_COUNT_MINB
+#define MIG_BATCH_MINB 3
 #endif
-__global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(const BatchParams bp) {
-    extern __shared__ AncRec s_anc_dyn[];  // bp.max_anc records per warp
-    __shared__ unsigned long long s_q[kWarps][kQueue];
-    __shared__ int4 s_cam[kWarps][4];
-    __shared__ HotVals s_hot[kWarps];
+// Dynamic shared memory per warp: a copy of the current tree's yaw rows (the per-node items read
+// them for every voxel; 12 ints and 9 floats per yaw), then bp.max_anc ancestor records.
+constexpr size_t kBatchYawBytes = (size_t)kNodeMaxK * (12 * sizeof(int) + 9 * sizeof(float));
+__global__ void __launch_bounds__(kBatchWarps * 32, MIG_BATCH_MINB) batch_kernel(const BatchParams bp) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ NodeWarp s_nw[kBatchWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *s_yi = reinterpret_cast<int *>(s_dyn + warp * kBatchYawBytes);
+    float *s_yf = reinterpret_cast<float *>(s_dyn + warp * kBatchYawBytes + (size_t)kNodeMaxK * 12 * sizeof(int));
+    int yaw_tree = -1;  // whose yaw rows the warp's copies hold
+    AncRec *anc = reinterpret_cast<AncRec *>(s_dyn + kBatchWarps * kBatchYawBytes) + warp * bp.max_anc;
+    NodeWarp &Q = s_nw[warp];
+    for (int t = lane; t < 2 * kNodeMaxK; t += 32) Q.cnt[t] = 0;
+    __syncwarp();
     if (bp.trace && blockIdx.x == 0 && threadIdx.x == 0) bp.trace[2 * (size_t)bp.n_segs_total] = global_ns();
-    int pos = 0;  // (lane 0) activation-log entry of this warp's previous item (entries only grow)
-    int cur_tree = -1;  // tree whose loop-live parameters s_hot[warp] holds
+    int pos = 0;                       // (lane 0) activation-log entry of this warp's previous item
+    int anc_tree = -1, anc_node = -1;  // whose ancestor records `anc` holds
+    int na = 0;
+    NodeStats nst;
+    uint32_t st_rays = 0, st_fine = 0, st_skip = 0;
     for (;;) {
         // lane 0 takes the next item number, waits (bounded) until it is activated, finds its
         // activation-log entry with relaxed loads, then one acquire fence orders this warp's
@@ -142,68 +149,80 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(cons
         local = __shfl_sync(0xffffffffu, local, 0);
         __syncwarp();
         if (seg < 0) break;
-        const int2 e = make_int2(0, seg);
-        const SegInfo sg = bp.segs[e.y];
-        const BatchTree &T = bp.trees[sg.tree];
-        const LevelParams &p = T.p;
-        const int idx = T.lvl_base + sg.level;
+        const SegInfo sg = bp.segs[seg];
+        const LevelParams &p = bp.trees[sg.tree].p;
         const int l0 = p.level_off[sg.level];
-        if (!sg.render) {
-            if (sg.tree != cur_tree) {
-                if (lane == 0) {
-                    HotVals h;
-                    h.g = p.grid.g;
-                    h.body = p.body;
-                    h.yawtab = p.yawtab;
-                    h.Tq = p.Tq;
-                    h.nx = p.grid.nx;
-                    h.ny = p.grid.ny;
-                    h.nz = p.grid.nz;
-                    h.W = p.W;
-                    h.H = p.H;
-                    h.tile_w = p.tile_w;
-                    h.pad0 = h.pad1 = 0;
-                    s_hot[warp] = h;
+        const size_t WH = (size_t)p.W * p.H;
+        if (sg.kind == kSegCast) {  // kBatchCastTiles consecutive tiles of one pair
+            const int tx = (p.W + kCastTileW - 1) / kCastTileW, tiles = tx * ((p.H + kCastTileH - 1) / kCastTileH);
+            const int ipp = (tiles + kBatchCastTiles - 1) / kBatchCastTiles;
+            const int ql = local / ipp, t0 = (local - ql * ipp) * kBatchCastTiles;
+            const uint8_t *bocc = p.grid.g + bocc_offset(p.grid.nx, p.grid.ny, p.grid.nz);
+            const uint8_t *sbocc = p.grid.g + sbocc_offset(p.grid.nx, p.grid.ny, p.grid.nz);
+            for (int tile = t0; tile < min(tiles, t0 + kBatchCastTiles); ++tile)
+                cast_item<false>(p, bocc, sbocc, l0, sg.q0 + ql, tile, tx, p.steps + (size_t)ql * WH, lane, st_rays,
+                                 st_fine, st_skip);
+        } else if (sg.kind == kSegVoxel) {
+            // the per-node item of the chunk's nodes, numbered as in the per-level kernel: groups of
+            // nodes whose step counts fit in L2 together, each node's slices and row blocks
+            const int K = p.K;
+            const int nb0 = sg.q0 / K, nn = (sg.q1 - sg.q0) / K;
+            const int yb_n = node_row_blocks(p.Tq);
+            const int per_node = (2 * ((int)(p.Tq >> 16) + 2) + 1) * yb_n;
+            const int grp = (int)max((size_t)1, min((size_t)nn, kStepsGroupBytes / ((size_t)K * WH * sizeof(uint16_t))));
+            const int g = local / (grp * per_node), r = local - g * grp * per_node;
+            const int gsz = min(grp, nn - g * grp);
+            const int rzy = r / gsz, ln = g * grp + r % gsz;
+            const int rank = rzy / yb_n, rb = rzy - rank * yb_n;
+            const int n = p.level_nodes[l0 + nb0 + ln];
+            NodeSlice S;
+            if (node_slice(p, n, rank, rb, yb_n, S)) {
+                if (sg.tree != anc_tree || n != anc_node) {
+                    na = node_ancestors(p, n, anc, lane);
+                    anc_tree = sg.tree;
+                    anc_node = n;
                 }
-                __syncwarp();
-                cur_tree = sg.tree;
+                if (sg.tree != yaw_tree) {
+                    __syncwarp();
+                    for (int t = lane; t < 12 * K; t += 32) s_yi[t] = p.yawtab[t];
+                    for (int t = lane; t < 9 * K; t += 32) s_yf[t] = p.yawf[t];
+                    __syncwarp();
+                    yaw_tree = sg.tree;
+                }
+                node_run<false>(p, S, s_yi, s_yf, p.steps + (size_t)ln * K * WH, Q, anc, na, lane, nst);
+                node_flush(p, n, Q, lane);  // before the item counts as done
             }
-            count_chunk<false>(p, HotStaged{&s_hot[warp]}, l0, local, s_anc_dyn + warp * bp.max_anc, s_q[warp],
-                                   s_cam[warp], lane);
-            int last = 0;
-            if (lane == 0) {
-                __threadfence();
-                last = atomicSub(bp.count_left + idx, 1) == 1;
+        } else {
+            const int groups = (int)((WH + 31) >> 5);
+            const int li = local / groups;
+            const int pix = (local - li * groups) * 32 + lane;
+            if (pix < (int)WH) {
+                const int n = p.level_nodes[l0 + li];
+                render_pixel(p, n, p.node[n], pix % p.W, pix / p.W);
             }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {  // every count item of (tree, level) is done: select the yaws
-                if (bp.trace && lane == 0) bp.trace[2 * (size_t)e.y + 1] = global_ns();
-                __threadfence();
+        }
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = atomicSub(bp.seg_left + seg, 1) == 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {  // every item of the segment is done
+            if (bp.trace && lane == 0) bp.trace[2 * (size_t)seg + 1] = global_ns();
+            __threadfence();
+            if (sg.select) {  // the level's last voxel segment: select its yaws
                 const int L = p.level_off[sg.level + 1] - l0;
                 for (int i = lane; i < L; i += 32) select_node(p, p.level_nodes[l0 + i]);
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) {
-                    if (bp.segs[e.y + 1].items > 0) activate(bp, e.y + 1);
-                    else level_done(bp, T, sg.tree, sg.level);
-                }
             }
-        } else {
-            const int WH = p.W * p.H;
-            const int groups = (WH + 31) >> 5;
-            const int li = local / groups;
-            const int pix = (local - li * groups) * 32 + lane;
-            if (pix < WH) {
-                const int n = p.level_nodes[l0 + li];
-                render_pixel(p, n, p.node[n], pix % p.W, pix / p.W);
-            }
-            __syncwarp();
             if (lane == 0) {
-                __threadfence();
-                if (atomicSub(bp.render_left + idx, 1) == 1) {
-                    if (bp.trace) bp.trace[2 * (size_t)e.y + 1] = global_ns();
-                    __threadfence();
-                    level_done(bp, T, sg.tree, sg.level);
+                if (sg.next >= 0) {
+                    activate(bp, sg.next);
+                } else {  // the tree is done: the next waiting tree starts
+                    const int i = atomicAdd(bp.pending_next, 1);
+                    if (i < bp.n_pending) activate(bp, bp.pending[i]);
                 }
             }
         }
@@ -212,17 +231,19 @@ __global__ void __launch_bounds__(kWarps * 32, MIG_BATCH_MINB) batch_kernel(cons
 
 }  // namespace
 
-size_t batch_dyn_smem(int max_anc) { return (size_t)kWarps * (size_t)std::max(1, max_anc) * sizeof(AncRec); }
+size_t batch_dyn_smem(int max_anc) {
+    return (size_t)kBatchWarps * (kBatchYawBytes + (size_t)std::max(1, max_anc) * sizeof(AncRec));
+}
 
 void launch_batch(const BatchParams &bp, int grid, cudaStream_t s) {
-    batch_kernel<<<grid, kWarps * 32, batch_dyn_smem(bp.max_anc), s>>>(bp);
+    batch_kernel<<<grid, kBatchWarps * 32, batch_dyn_smem(bp.max_anc), s>>>(bp);
 }
 
 int batch_ctas_per_sm() {
     int a = 0;
     const size_t smem = batch_dyn_smem(MIG_MAX_DEPTH);  // the worst case
     cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kBatchWarps * 32, batch_dyn_smem(16));
     cudaGetLastError();
     return std::max(1, a);
 }
@@ -260,6 +281,21 @@ struct mig_ctx::Batch {
 
 namespace {
 
+// Step-count buffer of each tree of a persistent launch: its largest level's (one cast and one voxel
+// segment per level keep every tree's chain of segments short), at most 1 GiB per tree and, scaled
+// down evenly, 24 GiB per launch; smaller buffers split levels into chunks that run one after another.
+#ifndef MIG_BATCH_TREE_STEPS
+#define MIG_BATCH_TREE_STEPS (1ull << 30)
+#endif
+constexpr size_t kBatchTreeStepsBytes = MIG_BATCH_TREE_STEPS;
+constexpr size_t kBatchStepsBytes = (size_t)24 << 30;
+// Trees in flight at once: the others wait, in order of decreasing work, until one finishes (fewer
+// trees interleave their items, so each tree's level chain waits less behind the others').
+#ifndef MIG_BATCH_IN_FLIGHT
+#define MIG_BATCH_IN_FLIGHT 16
+#endif
+constexpr int kBatchInFlight = MIG_BATCH_IN_FLIGHT;
+
 struct Carve {
     size_t off = 0;
     size_t take(size_t bytes) {
@@ -272,65 +308,95 @@ struct Carve {
 mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
     const int T = (int)items.size();
     if (T > kBatchMaxTrees) return fail(MIG_EINVAL, "batch_run: too many trees for one launch");
-    // ---- segments: per (tree, level) a count and a render segment; those outside a tree's
-    // launch range [level_lo, level_hi] have no items
-    int total_levels = 0;
-    std::vector<int> lvl_base(T);
-    for (int t = 0; t < T; ++t) {
-        lvl_base[t] = total_levels;
-        total_levels += items[t].plan.max_depth + 1;
-    }
-    const mig_tile_config tc = ctx->tiles;
-    std::vector<int> tiles_count(T), groups(T);
-    std::vector<SegInfo> segs(2 * (size_t)total_levels);
-    std::vector<int> cnt_left(total_levels, 0), rnd_left(total_levels, 0);
-    long long total = 0;
-    int n_nonempty = 0;
+    // ---- per tree: whole nodes per chunk, as many as its step-count buffer holds (at least one)
+    std::vector<int> chunk_nodes(T);
     for (int t = 0; t < T; ++t) {
         const BatchItem &it = items[t];
-        const int W = it.cam->W, H = it.cam->H;
-        tiles_count[t] = ((W + tc.tile_w - 1) / tc.tile_w) * ((H + tc.tile_h - 1) / tc.tile_h);
-        groups[t] = (W * H + 31) / 32;  // 32-pixel render items
-        for (int d = 0; d <= it.plan.max_depth; ++d) {
-            const bool in = d >= it.level_lo && d <= it.level_hi;
-            const int Ld = it.plan.level_off[d + 1] - it.plan.level_off[d];
-            const int nc = in ? Ld * it.cam->K * tiles_count[t] : 0;
-            const int nr = in ? it.plan.level_int[d] * groups[t] : 0;
-            const int id = lvl_base[t] + d;
-            segs[2 * (size_t)id] = SegInfo{t, d, 0, nc};
-            segs[2 * (size_t)id + 1] = SegInfo{t, d, 1, nr};
-            cnt_left[id] = nc;
-            rnd_left[id] = nr;
-            total += nc + nr;
-            n_nonempty += (nc > 0) + (nr > 0);
+        int Lmax = 1;
+        for (int d = it.level_lo; d <= it.level_hi; ++d)
+            Lmax = std::max(Lmax, it.plan.level_off[d + 1] - it.plan.level_off[d]);
+        const size_t node_bytes = (size_t)it.cam->K * it.cam->W * it.cam->H * sizeof(uint16_t);
+        chunk_nodes[t] = (int)std::max<size_t>(1, std::min<size_t>((size_t)Lmax, kBatchTreeStepsBytes / node_bytes));
+    }
+    {
+        size_t total_steps = 0;
+        for (int t = 0; t < T; ++t)
+            total_steps += (size_t)chunk_nodes[t] * items[t].cam->K * items[t].cam->W * items[t].cam->H * sizeof(uint16_t);
+        if (total_steps > kBatchStepsBytes) {
+            const double f = (double)kBatchStepsBytes / (double)total_steps;
+            for (int t = 0; t < T; ++t) chunk_nodes[t] = std::max(1, (int)(chunk_nodes[t] * f));
         }
     }
+    // ---- segments, tree by tree in level order: per chunk a cast and a voxel segment, then the
+    // level's render segment (if it has internal nodes); each segment's successor is the next one
+    // of its tree (the last voxel segment of a level selects the yaws first)
+    std::vector<SegInfo> segs;
+    std::vector<int> first_seg(T, -1);
+    long long total = 0;
+    for (int t = 0; t < T; ++t) {
+        const BatchItem &it = items[t];
+        const int K = it.cam->K, W = it.cam->W, H = it.cam->H;
+        const int cast_tiles = ((W + kCastTileW - 1) / kCastTileW) * ((H + kCastTileH - 1) / kCastTileH);
+        const int cast_ipp = (cast_tiles + kBatchCastTiles - 1) / kBatchCastTiles;  // cast items per pair
+        const int per_node = (2 * ((int)(range_q16(it.sensor.range_m, it.map->voxel) >> 16) + 2) + 1) *
+                             node_row_blocks(range_q16(it.sensor.range_m, it.map->voxel));
+        const int groups = (W * H + 31) / 32;  // 32-pixel render items
+        for (int d = it.level_lo; d <= it.level_hi; ++d) {
+            const int Ld = it.plan.level_off[d + 1] - it.plan.level_off[d];
+            if (first_seg[t] < 0) first_seg[t] = (int)segs.size();
+            for (int n0 = 0; n0 < Ld; n0 += chunk_nodes[t]) {
+                const int nc = std::min(chunk_nodes[t], Ld - n0);
+                const int q0 = n0 * K, q1 = (n0 + nc) * K;
+                segs.push_back(SegInfo{t, d, kSegCast, (q1 - q0) * cast_ipp, q0, q1, (int)segs.size() + 1, 0});
+                segs.push_back(SegInfo{t, d, kSegVoxel, nc * per_node, q0, q1, (int)segs.size() + 1, n0 + nc == Ld});
+            }
+            if (it.plan.level_int[d] > 0)
+                segs.push_back(SegInfo{t, d, kSegRender, it.plan.level_int[d] * groups, 0, 0, (int)segs.size() + 1, 0});
+        }
+        if (first_seg[t] >= 0) segs.back().next = -1;
+    }
+    std::vector<int> seg_left(segs.size());
+    for (size_t e = 0; e < segs.size(); ++e) {
+        seg_left[e] = segs[e].items;
+        total += segs[e].items;
+    }
     if (ctx->batch_debug_stall) {
-        // test hook: one level can never complete, so the waits behind it must run out
+        // test hook: one segment can never complete, so the waits behind it must run out
         for (int t = 0; t < T; ++t)
-            if (items[t].level_hi > items[t].level_lo) {
-                cnt_left[lvl_base[t] + items[t].level_lo] += 1;
+            if (first_seg[t] >= 0 && segs[first_seg[t]].next >= 0) {
+                seg_left[first_seg[t]] += 1;
                 break;
             }
     }
-    // the count segment of each tree's first launched level is ready from the start
+    // the first segment of each tree is ready from the start; the trees with the most work first
     std::vector<int2> log0;
     long long act_items = 0;
-    for (int t = 0; t < T; ++t) {
-        const int seg = 2 * (lvl_base[t] + items[t].level_lo);
-        if (items[t].level_lo > items[t].level_hi || segs[seg].items == 0) continue;
-        log0.push_back(make_int2((int)act_items, seg));
-        act_items += segs[seg].items;
+    std::vector<int> by_work(T);
+    for (int t = 0; t < T; ++t) by_work[t] = t;
+    std::stable_sort(by_work.begin(), by_work.end(), [&](int a, int b) {
+        return (long long)items[a].plan.n * items[a].cam->K * items[a].cam->W * items[a].cam->H >
+               (long long)items[b].plan.n * items[b].cam->K * items[b].cam->W * items[b].cam->H;
+    });
+    std::vector<int> pending;
+    for (int t : by_work) {
+        if (first_seg[t] < 0) continue;
+        if ((int)log0.size() >= kBatchInFlight) {
+            pending.push_back(first_seg[t]);
+            continue;
+        }
+        log0.push_back(make_int2((int)act_items, first_seg[t]));
+        act_items += segs[first_seg[t]].items;
     }
     if (total >= ((long long)1 << 31)) return fail(MIG_EINVAL, "tree_eval_batch: more than 2^31 work items in one batch");
-    const int log_cap = std::max(1, n_nonempty);
+    const int log_cap = std::max<int>(1, (int)segs.size());
     Carve cv;
     const size_t o_segs = cv.take(sizeof(SegInfo) * std::max<size_t>(1, segs.size()));
-    const size_t o_cl = cv.take(4 * (size_t)total_levels), o_rl = cv.take(4 * (size_t)total_levels);
+    const size_t o_left = cv.take(4 * std::max<size_t>(1, segs.size()));
+    const size_t o_pend = cv.take(4 * std::max<size_t>(1, pending.size())), o_pnext = cv.take(4);
     const size_t o_act = cv.take(8), o_work = cv.take(8);
     const size_t o_log = cv.take(8 * (size_t)log_cap), o_valid = cv.take(4 * (size_t)log_cap);
     struct TreeOff {
-        size_t node, ar, anc, loff, lint, lnodes, cnt, sel, out, arena;
+        size_t node, ar, anc, loff, lint, lnodes, cnt, sel, out, arena, steps;
     };
     std::vector<TreeOff> to(T);
     for (int t = 0; t < T; ++t) {
@@ -356,6 +422,7 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
     for (int t = 0; t < T; ++t) {
         to[t].sel = cv.take(4 * (size_t)items[t].plan.n);
         to[t].arena = cv.take(4 * (size_t)std::max(1, items[t].plan.n_internal) * items[t].cam->W * items[t].cam->H);
+        to[t].steps = cv.take((size_t)chunk_nodes[t] * items[t].cam->K * items[t].cam->W * items[t].cam->H * sizeof(uint16_t));
     }
     char *dev = nullptr;
     mig_status st = ctx_workspace(ctx, cv.off, (void **)&dev);
@@ -386,15 +453,12 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
         p.body = (const int4 *)it.cam->d_body;
         p.yawtab = it.cam->d_yaw;
+        p.yawf = it.cam->d_yawf;
         set_band(p, it.cam);
         p.W = it.cam->W;
         p.H = it.cam->H;
         p.K = it.cam->K;
         p.Tq = range_q16(it.sensor.range_m, m->voxel);
-        p.tile_w = tc.tile_w;
-        p.tile_h = tc.tile_h;
-        p.tiles_x = (p.W + tc.tile_w - 1) / tc.tile_w;
-        p.tiles = tiles_count[t];
         p.level_off = (const int32_t *)(dev + to[t].loff);
         p.level_int = (const int32_t *)(dev + to[t].lint);
         p.level_nodes = (const int32_t *)(dev + to[t].lnodes);
@@ -412,26 +476,30 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.lvl = 0;
         p.stats = nullptr;
         p.max_anc = std::max(1, pl.max_depth);
+        p.steps = (uint16_t *)(dev + to[t].steps);
+        p.steps_cap = chunk_nodes[t] * p.K;
         bt[t].p = p;
-        bt[t].lvl_base = lvl_base[t];
-        bt[t].n_levels = std::min(L, it.level_hi + 1);
     }
-    if (!segs.empty()) std::memcpy(host + o_segs, segs.data(), sizeof(SegInfo) * segs.size());
-    std::memcpy(host + o_cl, cnt_left.data(), 4 * (size_t)total_levels);
-    std::memcpy(host + o_rl, rnd_left.data(), 4 * (size_t)total_levels);
+    if (!segs.empty()) {
+        std::memcpy(host + o_segs, segs.data(), sizeof(SegInfo) * segs.size());
+        std::memcpy(host + o_left, seg_left.data(), 4 * segs.size());
+    }
+    if (!pending.empty()) std::memcpy(host + o_pend, pending.data(), 4 * pending.size());
+    *(int *)(host + o_pnext) = 0;
     *(unsigned long long *)(host + o_act) = ((unsigned long long)log0.size() << 40) | (unsigned long long)act_items;
     *(long long *)(host + o_work) = 0;
     if (!log0.empty()) std::memcpy(host + o_log, log0.data(), 8 * log0.size());
     for (size_t e = 0; e < log0.size(); ++e) ((int *)(host + o_valid))[e] = 1;
     bp.segs = (const SegInfo *)(dev + o_segs);
-    bp.n_levels_total = total_levels;
     bp.total_items = total;
     bp.act = (unsigned long long *)(dev + o_act);
     bp.log = (int2 *)(dev + o_log);
     bp.log_valid = (int *)(dev + o_valid);
     bp.work = (long long *)(dev + o_work);
-    bp.count_left = (int *)(dev + o_cl);
-    bp.render_left = (int *)(dev + o_rl);
+    bp.seg_left = (int *)(dev + o_left);
+    bp.pending = (const int *)(dev + o_pend);
+    bp.pending_next = (int *)(dev + o_pnext);
+    bp.n_pending = (int)pending.size();
     bp.status = (int *)(dev + o_status);
     bp.trace = tracing ? (unsigned long long *)(dev + o_trace) : nullptr;
     bp.n_segs_total = (int)segs.size();
@@ -507,7 +575,7 @@ mig_status batch_run(mig_ctx *ctx, std::vector<BatchItem> &items) {
             mig_trace_rec rec{};
             rec.tree = segs[i].tree;
             rec.level = segs[i].level;
-            rec.phase = segs[i].render;
+            rec.phase = segs[i].kind;
             rec.items = segs[i].items;
             rec.activated_us = tr[2 * i] ? (double)(long long)(tr[2 * i] - t0) * 1e-3 : 0.0;
             rec.done_us = tr[2 * i + 1] ? (double)(long long)(tr[2 * i + 1] - t0) * 1e-3 : -1.0;
@@ -608,6 +676,7 @@ mig_status batch_run_streams(mig_ctx *ctx, std::vector<BatchItem> &items) {
         p.grid = GridView{m->d_grid, m->nx, m->ny, m->nz, m->nbx, m->nby};
         p.body = (const int4 *)it.cam->d_body;
         p.yawtab = it.cam->d_yaw;
+        p.yawf = it.cam->d_yawf;
         set_band(p, it.cam);
         p.W = it.cam->W;
         p.H = it.cam->H;
@@ -799,14 +868,18 @@ extern "C" mig_status mig_tree_eval_batch(mig_ctx *ctx, int n_trees, const mig_t
     if (items.empty()) return MIG_OK;
     std::lock_guard<std::mutex> lk(ctx->mu);
     MIG_CUDA_TRY(cudaSetDevice(ctx->device));
-    bool per_mode_kernels = false;  // the interval and panoramic modes run on the stream-chain engine
+    // the persistent kernel runs the per-node owned-voxel pass of the sample modes; batches holding an
+    // interval or panoramic tree, a sensor outside the per-node pass (more than kNodeMaxK yaws, a
+    // frustum without an azimuth window) or a context counting ray by ray run on the stream chains
+    bool per_level_kernels = ctx->ray_count;
     for (auto &it : items) {
         mig_status st = ctx_camera(ctx, it.sensor, &it.cam);
         if (st != MIG_OK) return st;
         if (it.mode == MIG_MODE_PANORAMIC && (st = ctx_pano(ctx, it.cam)) != MIG_OK) return st;
-        per_mode_kernels |= it.mode == MIG_MODE_INTERVAL || it.mode == MIG_MODE_PANORAMIC;
+        per_level_kernels |= it.mode == MIG_MODE_INTERVAL || it.mode == MIG_MODE_PANORAMIC;
+        per_level_kernels |= !(it.cam->az_half > 0.f && it.cam->K <= kNodeMaxK);
     }
-    if (ctx->tiles.engine == 1 || per_mode_kernels) return batch_run_streams(ctx, items);
+    if (ctx->tiles.engine == 1 || per_level_kernels) return batch_run_streams(ctx, items);
     if ((int)items.size() <= kBatchMaxTrees) return batch_run(ctx, items);
     for (size_t s = 0; s < items.size(); s += kBatchMaxTrees) {  // one persistent launch per group
         std::vector<BatchItem> part(std::make_move_iterator(items.begin() + s),

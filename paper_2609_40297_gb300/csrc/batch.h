@@ -12,45 +12,58 @@
 
 namespace mig {
 
-// Per tree, in device memory: the tree's level parameters (pointers into the batch workspace)
-// and the index of its level 0 in the per-(tree, level) counter arrays.
+// Per tree, in device memory: the tree's level parameters (pointers into the batch workspace; the
+// step-count buffer of its chunks in p.steps).
 struct BatchTree {
     LevelParams p;
-    int lvl_base;
-    int n_levels;
 };
 
-// Work of one tree level is two segments: its count items (node, yaw, tile) and its render items
-// (internal node, 32 pixels). Segment id = 2 * (lvl_base[tree] + level) + phase. A segment becomes
-// ready (is "activated") when its dependencies are complete: the count segment of level d when
-// level d-1 is complete, the render segment when the level's yaws are selected. Activation
-// appends the segment to a log and gives it the next range of global item numbers; warps take
-// item numbers from one counter and only ever receive ready work.
+// Work of one tree level is a chain of segments: for each chunk of whole nodes (as many as the
+// tree's step-count buffer holds) a cast segment (items: (pair, 8x4 pixel tile)) and then a
+// voxel segment (items: (node, slice, 32-row block), the per-node pass), and at the end of the
+// level a render segment (items: (internal node, 32 pixels)). A segment becomes ready ("is
+// activated") when its predecessor is complete: a voxel segment after its chunk's cast, the next
+// chunk's cast after the voxel segment (they share the buffer), the render segment after the last
+// voxel segment and the yaw selection of the level, and the next level's first cast after the
+// render (the new depth buffers). Activation appends the segment to a log and gives it the next
+// range of global item numbers; warps take item numbers from one counter and only ever receive
+// ready work.
+enum SegKind { kSegCast = 0, kSegVoxel = 1, kSegRender = 2 };
 struct SegInfo {
     int tree;
     int level;
-    int render;
+    int kind;      // SegKind
     int items;
+    int q0, q1;    // cast / voxel: the chunk's (node, yaw) pairs [q0, q1) of the level (whole nodes)
+    int next;      // the segment activated when this one completes (-1: the tree is done; the next
+                   // waiting tree starts)
+    int select;    // voxel segment of the level's last chunk: select the level's yaws first
 };
 
 // Trees per persistent launch: their parameters travel in the kernel's parameter space (constant
 // bank, up to 32 KB), indexed by the warp-uniform tree number. Larger batches use several launches.
 constexpr int kBatchMaxTrees = 96;
+// 8x4-pixel cast tiles per work item of a cast segment (one item per warp takes one atomic).
+#ifndef MIG_BATCH_CAST_TILES
+#define MIG_BATCH_CAST_TILES 16
+#endif
+constexpr int kBatchCastTiles = MIG_BATCH_CAST_TILES;
 
 struct BatchParams {
     const SegInfo *segs;        // by segment id
-    int n_levels_total;
     long long total_items;      // of all segments of this launch
     unsigned long long *act;    // (log entries << 40) | activated items
     int2 *log;                  // per entry: (first item, segment id)
     int *log_valid;             // per entry: written (release flag)
     long long *work;            // global item counter
-    int *count_left;            // per (tree, level): count items not finished
-    int *render_left;           // per (tree, level): render items not finished
+    int *seg_left;              // per segment: items not finished
     int *status;                // [0] abort, [1] a wait timed out
     unsigned long long timeout_ns;
     unsigned long long *trace;  // NULL, or per segment (activated, completed) %globaltimer ns + kernel start
     int n_segs_total;
+    const int *pending;         // first segments of the trees not started at launch, in start order
+    int *pending_next;          // next entry of `pending` to start
+    int n_pending;
     int max_anc;                // ancestor records per warp: the deepest tree's depth (dynamic smem)
     BatchTree trees[kBatchMaxTrees];
 };

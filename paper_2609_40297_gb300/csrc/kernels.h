@@ -21,6 +21,7 @@ struct LevelParams {
     GridView grid;
     const int4 *body;        // H*W: body-frame ray (Q30) and camera z (Q30)
     const int32_t *yawtab;   // K*12: ck, sk, mu[3], mv[3], mz[3] (Q30, Q16)
+    const float *yawf;       // K*9: mu, mv, mz as floats / 2^16 (estimates only)
     int W, H, K;
     int64_t Tq;              // range, Q16 voxel units
     int tile_w, tile_h, tiles_x, tiles;  // count-pass tile (rays per warp work item)

@@ -55,8 +55,10 @@ struct Camera {
     int W = 0, H = 0, K = 0;
     std::vector<int32_t> body;  // H*W*4: bx, by, bz, dzc
     std::vector<int32_t> yaw;   // K*kYawRec
+    std::vector<float> yawf;    // K*9: each yaw's projection rows mu, mv, mz as floats (/ 2^16)
     int32_t *d_body = nullptr;
-    int32_t *d_yaw = nullptr;
+    int32_t *d_yaw = nullptr;   // the yaw table, then (same allocation) the float rows
+    const float *d_yawf = nullptr;
     // the frustum's extent about its yaw axis, for enumerating voxels once per node over all yaws
     // (conservative culling bounds, not result-deciding): tangents of the lowest and highest
     // elevation of a voxel centre that can project into the image, and the largest azimuth offset

@@ -196,6 +196,7 @@ mig_status admit(mig_server *s, Request &r) {
     p.grid = GridView{r.grid->ptr, m->nx, m->ny, m->nz, m->nbx, m->nby};
     p.body = (const int4 *)r.cam->d_body;
     p.yawtab = r.cam->d_yaw;
+    p.yawf = r.cam->d_yawf;
     set_band(p, r.cam);
     p.W = r.cam->W;
     p.H = r.cam->H;

@@ -17,8 +17,8 @@
 
 #include "kernels.h"
 #include "mig.h"
-#include "voxcount.cuh"
 #include "voxcount.h"
+#include "voxitems.cuh"
 
 namespace mig {
 
@@ -28,12 +28,6 @@ using namespace dev;
 
 constexpr int kCastWarps = 8;   // 256-thread CTAs, one ray per thread
 constexpr int kVoxWarps = 8;
-// The voxel passes hand out their work in groups of (node, yaw) pairs or nodes whose step counts
-// fit in this many bytes, so that the step counts the warps in flight read stay in L2.
-#ifndef MIG_STEPS_GROUP_BYTES
-#define MIG_STEPS_GROUP_BYTES (64u << 20)
-#endif
-constexpr size_t kStepsGroupBytes = MIG_STEPS_GROUP_BYTES;
 
 __device__ __forceinline__ int level_pairs(const LevelParams &p) {
     return (p.level_off[p.lvl + 1] - p.level_off[p.lvl]) * p.K;
@@ -41,7 +35,6 @@ __device__ __forceinline__ int level_pairs(const LevelParams &p) {
 
 // ------------------------------------------------------------------------------ cast kernel
 // Warp work item = (pair q of the chunk, 8x4 pixel tile); one ray per lane.
-constexpr int kCastTileW = 8, kCastTileH = 4;
 
 template <bool STATS>
 __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams p) {
@@ -60,20 +53,8 @@ __global__ void __launch_bounds__(kCastWarps * 32) cast_kernel(const LevelParams
          it += (long long)gridDim.x * kCastWarps) {
         const int tile = (int)(it % (tx * ty));
         const int ql = (int)(it / (tx * ty));
-        const int q = p.q0 + ql;
-        const int i = (tile % tx) * kCastTileW + (lane % kCastTileW), j = (tile / tx) * kCastTileH + lane / kCastTileW;
-        if (i >= p.W || j >= p.H) continue;
-        const int n = p.level_nodes[l0 + q / p.K];
-        const int k = q % p.K;
-        const int4 nd = p.node[n];
-        const int4 b = p.body[j * p.W + i];
-        const int32_t *yk = p.yawtab + k * 12;
-        int dx, dy, dz;
-        ray_dir(b, yk[0], yk[1], dx, dy, dz);
-        const uint32_t m = cast_hit<STATS>(p.grid.g, bocc, sbocc, p.grid.nx, p.grid.ny, p.grid.nz, nd.x, nd.y, nd.z, dx, dy,
-                                           dz, p.Tq, st_fine, st_skip);
-        p.steps[(size_t)ql * WH + (size_t)j * p.W + i] = (uint16_t)m;
-        if constexpr (STATS) ++st_rays;
+        cast_item<STATS>(p, bocc, sbocc, l0, p.q0 + ql, tile, tx, p.steps + (size_t)ql * WH, lane, st_rays, st_fine,
+                         st_skip);
     }
     if constexpr (STATS) {
         st_rays = __reduce_add_sync(0xffffffffu, st_rays);
@@ -95,24 +76,6 @@ struct VoxQueues {
     unsigned long long unk[64], own[64], smp[64];
 };
 
-// Appends the lanes' `take` entries `val` to queue q holding n entries (in lane order).
-__device__ __forceinline__ void q_push(unsigned long long *q, int &n, bool take, unsigned long long val,
-                                       unsigned lt_mask) {
-    const unsigned bal = __ballot_sync(0xffffffffu, take);
-    if (take) q[n + __popc(bal & lt_mask)] = val;
-    n += __popc(bal);
-    __syncwarp();
-}
-// Takes the first 32 entries of q (lane l gets entry l) and moves the rest to the front.
-__device__ __forceinline__ unsigned long long q_pop32(unsigned long long *q, int &n, int lane) {
-    const unsigned long long v = q[lane];
-    const unsigned long long rest = lane + 32 < n ? q[lane + 32] : 0ull;
-    __syncwarp();
-    if (lane + 32 < n) q[lane] = rest;
-    __syncwarp();
-    n -= 32;
-    return v;
-}
 
 // Warp work item = (pair q of the chunk, slice z of the node's range ball). Lanes take 32 rows
 // (y) of the slice at a time, clip each row to the frustum and the ball, and then load the rows'
@@ -320,121 +283,11 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) voxel_kernel(const LevelPar
     }
 }
 
-// Per-warp queues of the per-node pass: unknown voxels of the slice in the band, and counted voxels
-// with the mask of the yaws that count them.
-struct NodeQueues {
-    unsigned long long unk[64];    // x | y << 12
-    unsigned long long key[64];    // x | y << 12 | k_lo << 24 (first yaw of the mask's window)
-    unsigned long long mask[64];   // yaws (from k_lo) that count the voxel
-};
-
-// Stage C of the per-node pass: the ancestor test of 32 (or the last n) counted voxels, then their
-// per-yaw counts: every yaw of the voxel's mask gains an absolute count, and a marginal one unless
-// an ancestor observes the voxel.
-template <bool STATS>
-__device__ __forceinline__ void anc_stage_node(const LevelParams &p, NodeQueues &Q, int &nq, int lane,
-                                               const AncRec *anc, int na, int z, int K, int *s_cnt,
-                                               uint32_t &st_anc, uint32_t &st_reads, uint32_t &st_smp, bool full) {
-    const bool have = full || lane < nq;
-    unsigned long long key, mask;
-    if (full) {
-        key = Q.key[lane];
-        mask = Q.mask[lane];
-        const unsigned long long rk = lane + 32 < nq ? Q.key[lane + 32] : 0ull;
-        const unsigned long long rm = lane + 32 < nq ? Q.mask[lane + 32] : 0ull;
-        __syncwarp();
-        if (lane + 32 < nq) {
-            Q.key[lane] = rk;
-            Q.mask[lane] = rm;
-        }
-        __syncwarp();
-        nq -= 32;
-    } else {
-        key = Q.key[lane];
-        mask = Q.mask[lane];
-        nq = 0;
-    }
-    if (!have) return;
-    const int x = (int)(key & 0xFFF), y = (int)((key >> 12) & 0xFFF);
-    const bool obs = observed<STATS>(HotDirect{p}, anc, na, x, y, z, st_anc, st_reads);
-    int k = (int)(key >> 24);
-    while (mask) {
-        const int j = __ffsll((long long)mask) - 1;
-        mask &= mask - 1;
-        int kk = k + j;
-        kk -= kk >= K ? K : 0;
-        kk -= kk >= K ? K : 0;
-        atomicAdd(s_cnt + 2 * kk, 1);
-        if (!obs) atomicAdd(s_cnt + 2 * kk + 1, 1);
-        if constexpr (STATS) ++st_smp;
-    }
-}
-
 // ------------------------------------------------------------------------ per-node voxel kernel
 // The same counts with each voxel taken once per node for all yaws: the ancestor test of Sec. IV-B
 // does not depend on the node's own yaw, and a voxel lies in several yaws' frusta. Warp work item
-// = (node of the chunk, slice z of its range ball). Stage A: the slice's unknown voxels whose
-// centre's elevation is inside the frustum's band; stage B (one voxel per lane): for every yaw whose
-// frustum may hold it (azimuth window), its owner pixel (Eq. 5), the reach test by step index and
-// the exact visit test, giving a mask of the yaws that count it; stage C: the ancestor test once
-// per counted voxel, then the per-yaw counts in the warp's shared counters (added to the level's
-// counters at the end of the item).
-constexpr int kNodeMaxK = 64;  // yaws of the per-node pass (one mask word, per-warp counters)
-
-// Blocks of 32 rows covering one slice's rows of the range ball (at most 2 Rv + 3 rows, Rv = T + 2
-// voxels): the per-node pass hands out (node, slice, row block) items.
-__host__ __device__ inline int node_row_blocks(int64_t Tq) { return (2 * ((int)(Tq >> 16) + 2) + 3 + 31) / 32; }
-
-// Per-warp state of the per-node pass: queues of unknown voxels in the band and of counted voxels
-// with the mask of the yaws that count them, and the per-yaw (absolute, marginal) counters.
-struct NodeWarp {
-    unsigned long long unk[64];    // x | y << 12
-    unsigned long long key[64];    // x | y << 12 | k_lo << 24 (first yaw of the mask)
-    unsigned long long mask[64];   // yaws (from k_lo, cyclic) that count the voxel
-    unsigned long long vm[32];     // stage B: mask of the yaws counting each of the 32 voxels
-    unsigned long long xq[64];     // stage B: (voxel, yaw) pairs left to the exact visit test
-    int cnt[2 * kNodeMaxK];
-};
-
-// Stage C: the ancestor test of 32 (or the last n) counted voxels, then their per-yaw counts: every
-// yaw of the voxel's mask gains an absolute count, and a marginal one unless an ancestor observes it.
-template <bool STATS>
-__device__ __forceinline__ void node_anc_stage(const LevelParams &p, NodeWarp &Q, int &nq, int lane,
-                                               const AncRec *anc, int na, int z, int K, uint32_t &st_anc,
-                                               uint32_t &st_reads, uint32_t &st_smp, bool full) {
-    const bool have = full || lane < nq;
-    const unsigned long long key = Q.key[lane], mask0 = Q.mask[lane];
-    if (full) {
-        const unsigned long long rk = lane + 32 < nq ? Q.key[lane + 32] : 0ull;
-        const unsigned long long rm = lane + 32 < nq ? Q.mask[lane + 32] : 0ull;
-        __syncwarp();
-        if (lane + 32 < nq) {
-            Q.key[lane] = rk;
-            Q.mask[lane] = rm;
-        }
-        __syncwarp();
-        nq -= 32;
-    } else {
-        nq = 0;
-    }
-    if (have) {
-        const int x = (int)(key & 0xFFF), y = (int)((key >> 12) & 0xFFF);
-        const bool obs = observed<STATS>(HotDirect{p}, anc, na, x, y, z, st_anc, st_reads);
-        const int k0 = (int)(key >> 24);
-        unsigned long long mask = mask0;
-        while (mask) {
-            const int j = __ffsll((long long)mask) - 1;
-            mask &= mask - 1;
-            int kk = k0 + j;
-            kk -= kk >= K ? K : 0;
-            atomicAdd(Q.cnt + 2 * kk, 1);
-            if (!obs) atomicAdd(Q.cnt + 2 * kk + 1, 1);
-            if constexpr (STATS) ++st_smp;
-        }
-    }
-    __syncwarp();
-}
-
+// = (node of the chunk, slice z of its range ball, 32-row block of the slice), run by node_run
+// (voxitems.cuh); the warp's per-yaw counters go to the level's counters when its node changes.
 template <bool STATS>
 __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelParams p) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -442,7 +295,6 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
     __shared__ int s_yi[kNodeMaxK * 12];    // yaw rows: ck sk mu mv mz -
     __shared__ float s_yf[kNodeMaxK * 9];   // mu mv mz / 2^16
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const int K = p.K;
     AncRec *anc = reinterpret_cast<AncRec *>(s_dyn) + warp * p.max_anc;
     NodeWarp &Q = s_nw[warp];
@@ -454,33 +306,17 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
     for (int t = threadIdx.x; t < 9 * K; t += blockDim.x) s_yf[t] = (float)p.yawtab[(t / 9) * 12 + 2 + t % 9] * (1.0f / 65536.0f);
     for (int t = lane; t < 2 * K; t += 32) Q.cnt[t] = 0;
     __syncthreads();
-    const int Rv = (int)(p.Tq >> 16) + 2;
-    const int slices = 2 * Rv + 1;
+    const int slices = 2 * ((int)(p.Tq >> 16) + 2) + 1;
     const int nn = nb1 - nb0;
     const int yb_n = node_row_blocks(p.Tq);
     const int items = nn * slices * yb_n;
-    const float R = (float)p.Tq * (1.0f / 65536.0f) + 1.0f, R2 = R * R;
-    const int gnx = p.grid.nx, gny = p.grid.ny, gnz = p.grid.nz;
     const size_t WH = (size_t)p.W * p.H;
-    const float s16 = 1.0f / 65536.0f, yaw_scale = (float)K * 0.15915494309189535f;  // K / (2 pi)
-    const float Tv = (float)p.Tq * s16;  // the range in voxels
-    uint32_t st_cand = 0, st_unk = 0, st_visit = 0, st_anc = 0, st_reads = 0, st_smp = 0;
+    NodeStats st;
     int cur_node = -1, na = 0;
-    // the per-warp counters hold the counts of node cur_node until they are added to the level's
-    auto flush_counts = [&](int node) {
-        for (int t = lane; t < 2 * K; t += 32) {
-            const int v = Q.cnt[t];
-            if (v) {
-                atomicAdd(p.cnt + ((size_t)node * K + (t >> 1)) * 2 + (t & 1), v);
-                Q.cnt[t] = 0;
-            }
-        }
-        __syncwarp();
-    };
     // items are handed out one at a time from the launch's counter, in groups of nodes whose step
     // counts stay in L2 together; within a group every node's slice at its own height first (the
     // fullest), then outwards alternately above and below, and within a slice the 32-row blocks from
-    // the middle outwards
+    // the middle outwards. The warp's counters hold node cur_node's counts until the node changes.
     const int per_node = slices * yb_n;
     const int grp = (int)max((size_t)1, min((size_t)nn, kStepsGroupBytes / ((size_t)K * WH * sizeof(uint16_t))));
     for (;;) {
@@ -492,206 +328,31 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelPara
         const int gsz = min(grp, nn - g * grp);
         const int rzy = r / gsz, ln = g * grp + r % gsz;
         const int rank = rzy / yb_n, rb = rzy - rank * yb_n;
-        const int zi = Rv + ((rank & 1) ? (rank + 1) >> 1 : -(rank >> 1));
-        const int yblk = (yb_n - 1) / 2 + ((rb & 1) ? (rb + 1) >> 1 : -(rb >> 1));
         const int n = p.level_nodes[l0 + nb0 + ln];
-        const int4 nd = p.node[n];
-        const int v0x = nd.x >> 16, v0y = nd.y >> 16, v0z = nd.z >> 16;
-        const int z = v0z - Rv + zi;
-        if (z < 0 || z >= gnz) continue;
-        const float Pxf = (float)nd.x * s16 - 0.5f, Pyf = (float)nd.y * s16 - 0.5f, Pzf = (float)nd.z * s16 - 0.5f;
-        const float rz = small_int_to_float(z) - Pzf;
-        const float h2 = R2 - rz * rz;
-        if (h2 < 0.f) continue;
-        // no voxel of this slice can be in the band: above the slice's plane every centre's elevation is
-        // at least that of the outermost one, below it at most that of the outermost one
-        {
-            const float rho_max = sqrtf(h2);
-            const float eps = 0.01f * (rho_max + fabsf(rz)) + 0.05f;
-            if ((rz > 0.f && p.band_thi < 1e29f && rz > p.band_thi * rho_max + eps) ||
-                (rz < 0.f && p.band_tlo > -1e29f && rz < p.band_tlo * rho_max - eps))
-                continue;
-        }
-        const float hy = sqrtf(h2);
-        const int ylo = max(0, (int)floorf(Pyf - hy) - 1), yhi = min(gny - 1, (int)ceilf(Pyf + hy) + 1);
-        const int yb = ylo + 32 * yblk;  // this item's rows: block yblk of the slice's rows [ylo, yhi]
-        if (yb > yhi) continue;
-        if (n != cur_node) {  // the node's ancestors (Sec. IV-B), parent first
-            if (cur_node >= 0) flush_counts(cur_node);
-            const int2 ar = p.anc_range[n];
-            na = ar.y;
-            if (p.mode == MIG_MODE_ABSOLUTE) na = 0;
-            else if (p.mode == MIG_MODE_SINGLE_PARENT) na = min(na, 1);
-            na = min(na, p.max_anc);
-            fill_anc_records(p, ar, na, anc, lane);
+        NodeSlice S;
+        if (!node_slice(p, n, rank, rb, yb_n, S)) continue;
+        if (n != cur_node) {
+            if (cur_node >= 0) node_flush(p, cur_node, Q, lane);
+            na = node_ancestors(p, n, anc, lane);
             cur_node = n;
         }
-        const uint16_t *steps = p.steps + (size_t)ln * K * WH;
-        const int zq = (z << 16) + 32768 - nd.z;
-        int nu = 0, nq = 0;
-
-        // stage B: for 32 voxels (one per lane), the yaws that count them: every yaw whose frustum may
-        // hold the voxel (azimuth window) in turn gets its owner pixel (Eq. 5) and the reach test by
-        // step index; the visit test is decided by visit_surely where it can, else queued for the exact
-        // test, which runs 32 pairs at a time
-        auto yaw_stage = [&](bool full) {
-            const bool have = full || lane < nu;
-            const unsigned long long e = full ? q_pop32(Q.unk, nu, lane) : Q.unk[lane];
-            if (!full) nu = 0;
-            const int x = (int)(e & 0xFFF), y = (int)((e >> 12) & 0xFFF);
-            // the yaws whose frustum may hold the centre: psi_k within az_half of its azimuth (every
-            // yaw near the vertical axis)
-            const float fxr = small_int_to_float(x) - Pxf, fyr = small_int_to_float(y) - Pyf;
-            int klo = 0, nk = have ? K : 0;
-            if (have && fxr * fxr + fyr * fyr >= 4.0f && p.az_half < 3.0f) {
-                const float phi = atan2f(fyr, fxr);
-                const int a0 = (int)ceilf((phi - p.az_half) * yaw_scale);
-                const int a1 = (int)floorf((phi + p.az_half) * yaw_scale);
-                nk = max(0, min(K, a1 - a0 + 1));
-                klo = ((a0 % K) + K) % K;
-            }
-            Q.vm[lane] = 0ull;
-            int nx = 0;  // (voxel, yaw) pairs queued in Q.xq for the exact visit test
-            // exact visit test by the owner ray (event order of its DDA, range) of 32 queued pairs; the
-            // pairs that pass set their bit in the voxel's mask word
-            auto exact_stage = [&](bool xfull) {
-                const bool xh = xfull || lane < nx;
-                const unsigned long long q = xfull ? q_pop32(Q.xq, nx, lane) : Q.xq[lane];
-                if (!xfull) nx = 0;
-                if (xh) {
-                    const int qx = (int)(q & 0xFFF), qy = (int)((q >> 12) & 0xFFF);
-                    const int pix = (int)((q >> 24) & 0x3FFFFF), k = (int)((q >> 46) & 0x3F);
-                    const int j = (int)((q >> 52) & 0x3F), r = (int)(q >> 58);
-                    int dx, dy, dz;
-                    ray_dir(p.body[pix], s_yi[12 * k], s_yi[12 * k + 1], dx, dy, dz);
-                    if (visit_index(nd.x, nd.y, nd.z, dx, dy, dz, qx, qy, z, p.Tq) >= 0) atomicOr(Q.vm + r, 1ull << j);
-                }
-                __syncwarp();
-            };
-            __syncwarp();
-            const int rxq = (x << 16) + 32768 - nd.x, ryq = (y << 16) + 32768 - nd.y;
-            const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
-            unsigned long long mask = 0ull;
-            const int nk_max = __reduce_max_sync(0xffffffffu, (unsigned)nk);
-            for (int j = 0; j < nk_max; ++j) {
-                bool exact = false;
-                int pix = 0, k = 0;
-                if (j < nk) {
-                    k = klo + j;
-                    k -= k >= K ? K : 0;
-                    const int *rw = s_yi + 12 * k;
-                    const float *fw = s_yf + 9 * k;
-                    const int64_t Z = (int64_t)rw[8] * rxq + (int64_t)rw[9] * ryq + (int64_t)rw[10] * zq;
-                    if (Z > 0) {
-                        const int64_t U = (int64_t)rw[2] * rxq + (int64_t)rw[3] * ryq + (int64_t)rw[4] * zq;
-                        const int64_t V = (int64_t)rw[5] * rxq + (int64_t)rw[6] * ryq + (int64_t)rw[7] * zq;
-                        const float zi_ = __fdividef(1.0f, fmaf(fw[6], fxr, fmaf(fw[7], fyr, fw[8] * rz)));
-                        int pu, pv;
-                        if (pixel_in(U, Z, fmaf(fw[0], fxr, fmaf(fw[1], fyr, fw[2] * rz)) * zi_, p.W, pu) &&
-                            pixel_in(V, Z, fmaf(fw[3], fxr, fmaf(fw[4], fyr, fw[5] * rz)) * zi_, p.H, pv)) {
-                            pix = pv * p.W + pu;
-                            if (man < (int)__ldg(steps + (size_t)k * WH + pix)) {  // before the owner ray's hit
-                                if constexpr (STATS) ++st_visit;
-                                int dx, dy, dz;
-                                ray_dir(p.body[pix], rw[0], rw[1], dx, dy, dz);
-                                if (visit_surely(fxr, fyr, rz, dx, dy, dz, Tv)) mask |= 1ull << j;
-                                else exact = true;
-                            }
-                        }
-                    }
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, exact);
-                if (exact)
-                    Q.xq[nx + __popc(bal & lt_mask)] = (unsigned long long)x | ((unsigned long long)y << 12) |
-                                                       ((unsigned long long)pix << 24) | ((unsigned long long)k << 46) |
-                                                       ((unsigned long long)j << 52) | ((unsigned long long)lane << 58);
-                nx += __popc(bal);
-                __syncwarp();
-                if (nx >= 32) exact_stage(true);
-            }
-            if (nx > 0) exact_stage(false);
-            mask |= Q.vm[lane];
-            const bool put = have && mask != 0ull;
-            const unsigned bal = __ballot_sync(0xffffffffu, put);
-            if (put) {
-                const int slot = nq + __popc(bal & lt_mask);
-                Q.key[slot] = (unsigned long long)x | ((unsigned long long)y << 12) | ((unsigned long long)klo << 24);
-                Q.mask[slot] = mask;
-            }
-            nq += __popc(bal);
-            __syncwarp();
-            if (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
-        };
-
-        {
-            const int y = yb + lane;
-            int xa = 0, len = 0;
-            if (y <= yhi) {
-                const float ry = small_int_to_float(y) - Pyf;
-                const float hx2 = h2 - ry * ry;
-                if (hx2 >= 0.f) {
-                    const float hx = sqrtf(hx2);
-                    xa = max(0, (int)floorf(Pxf - hx) - 1);
-                    len = max(0, min(gnx - 1, (int)ceilf(Pxf + hx) + 1) - xa + 1);
-                }
-            }
-            int incl = len;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += v;
-            }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            for (int base = 0; base < tot; base += 32) {
-                const int f = base + lane;
-                int r = 0;
-#pragma unroll
-                for (int sh = 16; sh >= 1; sh >>= 1) {
-                    const int cv = __shfl_sync(0xffffffffu, incl, r + sh - 1);
-                    if (cv <= f) r += sh;
-                }
-                r = min(r, 31);
-                const int rxa = __shfl_sync(0xffffffffu, xa, r);
-                const int rstart = __shfl_sync(0xffffffffu, incl - len, r);
-                bool unk = false;
-                int x = 0;
-                if (f < tot) {
-                    x = rxa + (f - rstart);
-                    if constexpr (STATS) ++st_cand;
-                    const uint32_t addr = ((uint32_t)z * (uint32_t)gny + (uint32_t)(yb + r)) * (uint32_t)gnx + (uint32_t)x;
-                    if (load_code(p.grid.g, addr, p.grid, p.bounds_err) == kUnknown) {
-                        // inside the frustum's elevation band (widened; exact tests follow)
-                        const float fx = small_int_to_float(x) - Pxf, fy = small_int_to_float(yb + r) - Pyf;
-                        const float rho = sqrtf(fx * fx + fy * fy);
-                        const float eps = 0.01f * (rho + fabsf(rz)) + 0.05f;
-                        unk = (p.band_thi >= 1e29f || rz <= p.band_thi * rho + eps) &&
-                              (p.band_tlo <= -1e29f || rz >= p.band_tlo * rho - eps);
-                    }
-                    if constexpr (STATS) st_unk += unk;
-                }
-                q_push(Q.unk, nu, unk, (unsigned long long)x | ((unsigned long long)(yb + r) << 12), lt_mask);
-                if (nu >= 32) yaw_stage(true);
-            }
-        }
-        if (nu > 0) yaw_stage(false);
-        while (nq >= 32) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, true);
-        if (nq > 0) node_anc_stage<STATS>(p, Q, nq, lane, anc, na, z, K, st_anc, st_reads, st_smp, false);
+        node_run<STATS>(p, S, s_yi, s_yf, p.steps + (size_t)ln * K * WH, Q, anc, na, lane, st);
     }
-    if (cur_node >= 0) flush_counts(cur_node);
+    if (cur_node >= 0) node_flush(p, cur_node, Q, lane);
     if constexpr (STATS) {
-        st_cand = __reduce_add_sync(0xffffffffu, st_cand);
-        st_unk = __reduce_add_sync(0xffffffffu, st_unk);
-        st_visit = __reduce_add_sync(0xffffffffu, st_visit);
-        st_anc = __reduce_add_sync(0xffffffffu, st_anc);
-        st_reads = __reduce_add_sync(0xffffffffu, st_reads);
-        st_smp = __reduce_add_sync(0xffffffffu, st_smp);
+        st.cand = __reduce_add_sync(0xffffffffu, st.cand);
+        st.unk = __reduce_add_sync(0xffffffffu, st.unk);
+        st.visit = __reduce_add_sync(0xffffffffu, st.visit);
+        st.anc = __reduce_add_sync(0xffffffffu, st.anc);
+        st.reads = __reduce_add_sync(0xffffffffu, st.reads);
+        st.smp = __reduce_add_sync(0xffffffffu, st.smp);
         if (lane == 0) {
-            atomicAdd(p.stats + 11, (unsigned long long)st_cand);
-            atomicAdd(p.stats + 12, (unsigned long long)st_unk);
-            atomicAdd(p.stats + 13, (unsigned long long)st_visit);
-            atomicAdd(p.stats + 14, (unsigned long long)st_smp);
-            atomicAdd(p.stats + 15, (unsigned long long)st_anc);
-            atomicAdd(p.stats + 16, (unsigned long long)st_reads);
+            atomicAdd(p.stats + 11, (unsigned long long)st.cand);
+            atomicAdd(p.stats + 12, (unsigned long long)st.unk);
+            atomicAdd(p.stats + 13, (unsigned long long)st.visit);
+            atomicAdd(p.stats + 14, (unsigned long long)st.smp);
+            atomicAdd(p.stats + 15, (unsigned long long)st.anc);
+            atomicAdd(p.stats + 16, (unsigned long long)st.reads);
         }
     }
 }

@@ -169,10 +169,8 @@ MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, const uint8_t *s
         nz = n0z + ((uint32_t)cz << 16);
         m = (uint32_t)(cx + cy + cz);
     };
-    int occ_super = -1;  // the super-brick last found to hold an occupied voxel (not read again)
     for (;;) {
-        const int si = ((vz >> 5) * nsy + (vy >> 5)) * nsx + (vx >> 5);
-        if (sbocc && si != occ_super && !ld_u8(sbocc + si)) {
+        if (sbocc && !ld_u8(sbocc + ((vz >> 5) * nsy + (vy >> 5)) * nsx + (vx >> 5))) {
             // super-brick walk: per axis the crossing index (from the start) that leaves the current
             // super-brick, until the ray enters one that holds an occupied voxel
             int ex = cell_exit_crossing(vx, v0x, sx, gnx, kOccSuperShift), ey = cell_exit_crossing(vy, v0y, sy, gny, kOccSuperShift),
@@ -197,13 +195,11 @@ MIG_HD uint32_t cast_hit(const uint8_t *g, const uint8_t *bocc, const uint8_t *s
                 ez = e == 2 ? nEe : ez;
                 if (ld_u8(sbocc + (bz * nsy + by) * nsx + bx)) {
                     enter(NE, AE, e, Ee, ox, oy, oz);
-                    occ_super = (bz * nsy + by) * nsx + bx;
                     break;
                 }
             }
             continue;
         }
-        occ_super = si;
         if (!bocc || ld_u8(bocc + ((vz >> 3) * nby + (vy >> 3)) * nbx + (vx >> 3))) {
             // voxel walk inside a brick that holds an occupied voxel, up to its faces: bnx.. = face
             // distance of the crossing that leaves the brick along each axis

@@ -146,9 +146,9 @@ def spread(xs):
 # -------------------------------------------------------------------- kernels and roofline
 # Source files whose code (comments and blank lines removed) an ncu summary is tied to.
 KERNEL_SOURCES = {
-    "cast_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
-    "voxel_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
-    "node_kernel": ("voxcount.cu", "voxcount.cuh", "dev_path.cuh", "kernels.h"),
+    "cast_kernel": ("voxcount.cu", "voxcount.cuh", "voxitems.cuh", "dev_path.cuh", "kernels.h"),
+    "voxel_kernel": ("voxcount.cu", "voxcount.cuh", "voxitems.cuh", "dev_path.cuh", "kernels.h"),
+    "node_kernel": ("voxcount.cu", "voxcount.cuh", "voxitems.cuh", "dev_path.cuh", "kernels.h"),
     "count_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
     "render_kernel": ("kernels.cu", "kernels.h", "dev_path.cuh"),
 }

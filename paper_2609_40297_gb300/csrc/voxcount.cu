@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kVoxWarps * 32, 3) voxel_kernel(const LevelPar
 // = (node of the chunk, slice z of its range ball, 32-row block of the slice), run by node_run
 // (voxitems.cuh); the warp's per-yaw counters go to the level's counters when its node changes.
 template <bool STATS>
-__global__ void __launch_bounds__(kVoxWarps * 32, 3) node_kernel(const LevelParams p) {
+__global__ void __launch_bounds__(kVoxWarps * 32, 4) node_kernel(const LevelParams p) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ NodeWarp s_nw[kVoxWarps];
     __shared__ int s_yi[kNodeMaxK * 12];    // yaw rows: ck sk mu mv mz -

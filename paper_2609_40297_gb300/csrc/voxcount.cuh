@@ -65,6 +65,15 @@ MIG_HD float fast_div(uint32_t a, uint32_t b) {
 #endif
 }
 
+// a / b in float, approximately (the device's fast division; relative error about 1e-7).
+MIG_HD float fast_divf(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
 // Number of crossings j in [0, jmax] of an axis (face distances nb + j 2^16, speed adb, index b)
 // that come before the event (NE / AE, e). The caller guarantees that crossing jmax does not, so
 // the answer is at most jmax. tE = NE / AE in float gives a first guess; exact comparisons fix it.
@@ -301,21 +310,23 @@ MIG_HD int visit_index(int Px, int Py, int Pz, int dx, int dy, int dz, int x, in
     return c[0] + c[1] + c[2];
 }
 
-// A sufficient condition for visit_index >= 0, in float: the ray (origin P, direction d, Q30) passes
-// within 0.48 voxel of the voxel's centre c (cx, cy, cz: c - P in voxels) at a distance s along it with
-// 0.01 <= s <= T - 0.01 (T in voxels). The ray point there lies in the voxel's inscribed ball, so the
-// ray crosses the voxel's interior; between crossings the walk is in the voxel that holds the ray
-// point, so it visits the voxel, before T, and inside the grid (a box, which holds the origin and the
-// voxel). The float rounding of c (below 1e-3 voxel for grids up to 4096) and of the products
-// (relative 1e-6) stays far inside the 0.02 and 0.01 voxel margins. False says nothing.
+// A sufficient condition for visit_index >= 0, in float: the point of the ray (origin P, direction
+// d, Q30) nearest to the voxel's centre c (cx, cy, cz: c - P in voxels) lies inside the voxel, at
+// least 0.01 voxel from every face, at a distance s along the ray with 0.01 <= s <= T - 0.01 (T in
+// voxels). Then the ray crosses the voxel's interior there; between crossings the walk is in the
+// voxel that holds the ray point, so it visits the voxel, before T, and inside the grid (a box,
+// which holds the origin and the voxel). The float rounding of c (below 1e-3 voxel for grids up to
+// 4096) and of the products and the quotient (relative 1e-6 of at most 1030 voxels) stays inside
+// the 0.01 voxel margins. False says nothing.
 MIG_HD bool visit_surely(float cx, float cy, float cz, int dx, int dy, int dz, float Tv) {
     const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
     const float dd = fx * fx + fy * fy + fz * fz;
     const float cd = cx * fx + cy * fy + cz * fz;
-    const float ex = cy * fz - cz * fy, ey = cz * fx - cx * fz, ez = cx * fy - cy * fx;
-    const float e2 = ex * ex + ey * ey + ez * ez;  // (distance to the line)^2 |d|^2
-    const float s = cd * 1073741824.0f;            // distance along the ray times |d|^2 (|d| = 2^30)
-    return e2 < 0.2304f * dd && s >= 0.01f * dd && s <= (Tv - 0.01f) * dd;
+    const float lam = fast_divf(cd, dd);  // the nearest point is P + lam d
+    const float ex = lam * fx - cx, ey = lam * fy - cy, ez = lam * fz - cz;
+    const float s = cd * 1073741824.0f;  // distance along the ray times |d|^2 (|d| = 2^30)
+    return fabsf(ex) < 0.49f && fabsf(ey) < 0.49f && fabsf(ez) < 0.49f && s >= 0.01f * dd &&
+           s <= (Tv - 0.01f) * dd;
 }
 
 // One half-space a rx + b ry + c rz > 0 of the voxel-centre offsets r (voxel units, float),

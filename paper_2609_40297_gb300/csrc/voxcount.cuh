@@ -329,6 +329,34 @@ MIG_HD bool visit_surely(float cx, float cy, float cz, int dx, int dy, int dz, f
            s <= (Tv - 0.01f) * dd;
 }
 
+// Eq. 5's pixel of a voxel centre from float projection rows, with a proven error bound: returns 1
+// when the exact test (Z > 0, pixel (floor(U/Z), floor(V/Z)) inside the image) surely passes with
+// pixel (pu, pv), 0 when it surely fails, -1 when the float values are too close to a pixel boundary
+// or to Z = 0 to tell (the caller runs the exact test). w: the yaw's rows mu, mv, mz as floats
+// divided by 2^16 (each within relative 2^-24 of the exact row); ex, ey, ez: the centre's offset
+// from the camera in voxels, converted from its exact Q16 value (within relative 2^-24). Each float
+// sum of three products is then within 5 u S of the exact one (u = 2^-24, S = the row's L1 norm
+// times the largest offset), so with eU, eV, eZ = norm * 6.5 u (rinf + 1):
+//   |Z - Zf| <= eZ, and for Zf > 2 eZ, |U/Z - Uf/Zf| <= 2 (eU + |Uf/Zf| eZ) / Zf;
+// the fast reciprocal and the product add at most 3.1e-7 |u|, covered by the 1e-6 terms.
+MIG_HD int pixel_fast(const float *w, float ex, float ey, float ez, float rinf, int W, int H, int &pu, int &pv) {
+    const float c = 3.9e-7f * (rinf + 1.0f);  // 6.5 * 2^-24 * (rinf + 1)
+    const float zf = fmaf(w[6], ex, fmaf(w[7], ey, w[8] * ez));
+    const float e_z = (fabsf(w[6]) + fabsf(w[7]) + fabsf(w[8])) * c;
+    if (!(zf > 2.0f * e_z)) return zf < -e_z ? 0 : -1;
+    const float zi = fast_divf(1.0f, zf);
+    const float u = fmaf(w[0], ex, fmaf(w[1], ey, w[2] * ez)) * zi;
+    const float v = fmaf(w[3], ex, fmaf(w[4], ey, w[5] * ez)) * zi;
+    const float e_u = 2.0f * zi * ((fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2])) * c + fabsf(u) * e_z) + 1e-6f * fabsf(u) + 1e-6f;
+    const float e_v = 2.0f * zi * ((fabsf(w[3]) + fabsf(w[4]) + fabsf(w[5])) * c + fabsf(v) * e_z) + 1e-6f * fabsf(v) + 1e-6f;
+    if (u + e_u < 0.0f || u - e_u >= (float)W || v + e_v < 0.0f || v - e_v >= (float)H) return 0;
+    const float fu = floorf(u - e_u), fv = floorf(v - e_v);
+    if (fu < 0.0f || fv < 0.0f || floorf(u + e_u) != fu || floorf(v + e_v) != fv) return -1;
+    pu = (int)fu;
+    pv = (int)fv;
+    return 1;
+}
+
 // One half-space a rx + b ry + c rz > 0 of the voxel-centre offsets r (voxel units, float),
 // shifted outwards by one voxel (its L1 coefficient norm), narrows a row's [lo, hi] of rx. The
 // shift covers the float rounding of the row terms, so no voxel inside the half-space is dropped;

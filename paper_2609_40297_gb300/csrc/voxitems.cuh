@@ -203,6 +203,7 @@ __device__ __forceinline__ void node_run(const LevelParams &p, const NodeSlice &
     const int z = S.z, yb = S.yb, yhi = S.yhi;
     const float Pxf = S.Pxf, Pyf = S.Pyf, rz = S.rz, h2 = S.h2;
     const int zq = (z << 16) + 32768 - nd.z;
+    const float ez = (float)zq * (1.0f / 65536.0f);
     int nu = 0, nq = 0;
 
     // stage B: for 32 voxels (one per lane), the yaws that count them: every yaw whose frustum may
@@ -246,6 +247,9 @@ __device__ __forceinline__ void node_run(const LevelParams &p, const NodeSlice &
         __syncwarp();
         const int rxq = (x << 16) + 32768 - nd.x, ryq = (y << 16) + 32768 - nd.y;
         const int man = abs(x - v0x) + abs(y - v0y) + abs(z - v0z);
+        // the centre's offset from the camera in voxels, from its exact Q16 value
+        const float ex = (float)rxq * (1.0f / 65536.0f), ey = (float)ryq * (1.0f / 65536.0f);
+        const float rinf = fmaxf(fabsf(ex), fmaxf(fabsf(ey), fabsf(ez)));
         unsigned long long mask = 0ull;
         const int nk_max = __reduce_max_sync(0xffffffffu, (unsigned)nk);
         for (int j = 0; j < nk_max; ++j) {
@@ -256,22 +260,29 @@ __device__ __forceinline__ void node_run(const LevelParams &p, const NodeSlice &
                 k -= k >= K ? K : 0;
                 const int *rw = s_yi + 12 * k;
                 const float *fw = s_yf + 9 * k;
-                const int64_t Z = (int64_t)rw[8] * rxq + (int64_t)rw[9] * ryq + (int64_t)rw[10] * zq;
-                if (Z > 0) {
-                    const int64_t U = (int64_t)rw[2] * rxq + (int64_t)rw[3] * ryq + (int64_t)rw[4] * zq;
-                    const int64_t V = (int64_t)rw[5] * rxq + (int64_t)rw[6] * ryq + (int64_t)rw[7] * zq;
-                    const float zi_ = __fdividef(1.0f, fmaf(fw[6], fxr, fmaf(fw[7], fyr, fw[8] * rz)));
-                    int pu, pv;
-                    if (pixel_in(U, Z, fmaf(fw[0], fxr, fmaf(fw[1], fyr, fw[2] * rz)) * zi_, p.W, pu) &&
-                        pixel_in(V, Z, fmaf(fw[3], fxr, fmaf(fw[4], fyr, fw[5] * rz)) * zi_, p.H, pv)) {
-                        pix = pv * p.W + pu;
-                        if (man < (int)__ldg(steps + (size_t)k * WH + pix)) {  // before the owner ray's hit
-                            if constexpr (STATS) ++st.visit;
-                            int dx, dy, dz;
-                            ray_dir(p.body[pix], rw[0], rw[1], dx, dy, dz);
-                            if (visit_surely(fxr, fyr, rz, dx, dy, dz, Tv)) mask |= 1ull << j;
-                            else exact = true;
-                        }
+                // the owner pixel (Eq. 5): from the float rows where their error bound decides it,
+                // else by the exact integer projection
+                int pu = 0, pv = 0;
+                int in = pixel_fast(fw, ex, ey, ez, rinf, p.W, p.H, pu, pv);
+                if (in < 0) {
+                    in = 0;
+                    const int64_t Z = (int64_t)rw[8] * rxq + (int64_t)rw[9] * ryq + (int64_t)rw[10] * zq;
+                    if (Z > 0) {
+                        const int64_t U = (int64_t)rw[2] * rxq + (int64_t)rw[3] * ryq + (int64_t)rw[4] * zq;
+                        const int64_t V = (int64_t)rw[5] * rxq + (int64_t)rw[6] * ryq + (int64_t)rw[7] * zq;
+                        const float zi_ = __fdividef(1.0f, fmaf(fw[6], ex, fmaf(fw[7], ey, fw[8] * ez)));
+                        in = pixel_in(U, Z, fmaf(fw[0], ex, fmaf(fw[1], ey, fw[2] * ez)) * zi_, p.W, pu) &&
+                             pixel_in(V, Z, fmaf(fw[3], ex, fmaf(fw[4], ey, fw[5] * ez)) * zi_, p.H, pv);
+                    }
+                }
+                if (in) {
+                    pix = pv * p.W + pu;
+                    if (man < (int)__ldg(steps + (size_t)k * WH + pix)) {  // before the owner ray's hit
+                        if constexpr (STATS) ++st.visit;
+                        int dx, dy, dz;
+                        ray_dir(p.body[pix], rw[0], rw[1], dx, dy, dz);
+                        if (visit_surely(ex, ey, ez, dx, dy, dz, Tv)) mask |= 1ull << j;
+                        else exact = true;
                     }
                 }
             }

@@ -339,10 +339,12 @@ MIG_HD bool visit_surely(float cx, float cy, float cz, int dx, int dy, int dz, f
 // times the largest offset), so with eU, eV, eZ = norm * 6.5 u (rinf + 1):
 //   |Z - Zf| <= eZ, and for Zf > 2 eZ, |U/Z - Uf/Zf| <= 2 (eU + |Uf/Zf| eZ) / Zf;
 // the fast reciprocal and the product add at most 3.1e-7 |u|, covered by the 1e-6 terms.
-MIG_HD int pixel_fast(const float *w, float ex, float ey, float ez, float rinf, int W, int H, int &pu, int &pv) {
+// zf, e_z: the float camera depth (voxels) and its error bound, for a depth comparison that follows.
+MIG_HD int pixel_fast(const float *w, float ex, float ey, float ez, float rinf, int W, int H, int &pu, int &pv,
+                      float &zf, float &e_z) {
     const float c = 3.9e-7f * (rinf + 1.0f);  // 6.5 * 2^-24 * (rinf + 1)
-    const float zf = fmaf(w[6], ex, fmaf(w[7], ey, w[8] * ez));
-    const float e_z = (fabsf(w[6]) + fabsf(w[7]) + fabsf(w[8])) * c;
+    zf = fmaf(w[6], ex, fmaf(w[7], ey, w[8] * ez));
+    e_z = (fabsf(w[6]) + fabsf(w[7]) + fabsf(w[8])) * c;
     if (!(zf > 2.0f * e_z)) return zf < -e_z ? 0 : -1;
     const float zi = fast_divf(1.0f, zf);
     const float u = fmaf(w[0], ex, fmaf(w[1], ey, w[2] * ez)) * zi;

@@ -59,6 +59,53 @@ struct NodeStats {
     uint32_t cand = 0, unk = 0, visit = 0, anc = 0, reads = 0, smp = 0;
 };
 
+// Sec. IV-B's ancestor test of voxel (x, y, z) (observed iff some ancestor sees its centre at camera
+// depth z <= D), deciding each ancestor's pixel and the depth comparison from the float rows where
+// their proven error bounds do (pixel_fast), else with the exact integers of the per-ray test.
+template <bool STATS>
+__device__ __forceinline__ bool observed_fast(const LevelParams &p, const AncRec *anc, int na, int x, int y, int z,
+                                              uint32_t &st_anc, uint32_t &st_reads) {
+    for (int a = 0; a < na; ++a) {
+        const AncRec &A = anc[a];
+        const int ax = (x << 16) + 32768 - A.px, ay = (y << 16) + 32768 - A.py, az = (z << 16) + 32768 - A.pz;
+        if constexpr (STATS) ++st_anc;
+        const float ex = (float)ax * (1.0f / 65536.0f), ey = (float)ay * (1.0f / 65536.0f);
+        const float ez = (float)az * (1.0f / 65536.0f);
+        const float rinf = fmaxf(fabsf(ex), fmaxf(fabsf(ey), fabsf(ez)));
+        int pu = 0, pv = 0;
+        float zf, e_z;
+        const int in = pixel_fast(A.m, ex, ey, ez, rinf, p.W, p.H, pu, pv, zf, e_z);
+        if (in == 0) continue;
+        const int4 *row = reinterpret_cast<const int4 *>(p.yawtab + A.yaw * 12);
+        if (in > 0) {
+            const uint32_t D = __ldg(A.D + pv * p.W + pu);
+            if constexpr (STATS) ++st_reads;
+            // z <= D  <=>  Z < (D + 1) / 2^16 (voxels); lim within relative 2^-23 of that
+            const float lim = ((float)D + 1.0f) * (1.0f / 65536.0f);
+            if (zf + e_z < lim * (1.0f - 2.4e-7f)) return true;
+            if (zf - e_z >= lim * (1.0f + 2.4e-7f)) continue;
+            const int4 r2 = __ldg(row + 2);
+            const int64_t Za = (int64_t)r2.x * ax + (int64_t)r2.y * ay + (int64_t)r2.z * az;
+            if (Za < (((int64_t)D + 1) << 16)) return true;
+            continue;
+        }
+        // near a pixel boundary or Z = 0: the exact projection (Eq. 5)
+        const int4 r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2);  // ck sk mu0 mu1 | mu2 mv0 mv1 mv2 | mz0 mz1 mz2 -
+        const int64_t Za = (int64_t)r2.x * ax + (int64_t)r2.y * ay + (int64_t)r2.z * az;
+        if (Za <= 0) continue;
+        const int64_t Ua = (int64_t)r0.z * ax + (int64_t)r0.w * ay + (int64_t)r1.x * az;
+        const int64_t Va = (int64_t)r1.y * ax + (int64_t)r1.z * ay + (int64_t)r1.w * az;
+        const float zi = __fdividef(1.0f, zf);
+        const float uf = fmaf(A.m[0], ex, fmaf(A.m[1], ey, A.m[2] * ez)) * zi;
+        const float vf = fmaf(A.m[3], ex, fmaf(A.m[4], ey, A.m[5] * ez)) * zi;
+        if (!pixel_in(Ua, Za, uf, p.W, pu) || !pixel_in(Va, Za, vf, p.H, pv)) continue;
+        const uint32_t D = __ldg(A.D + pv * p.W + pu);
+        if constexpr (STATS) ++st_reads;
+        if (Za < (((int64_t)D + 1) << 16)) return true;
+    }
+    return false;
+}
+
 // Stage C: the ancestor test of 32 (or the last n) counted voxels, then their per-yaw counts: every
 // yaw of the voxel's mask gains an absolute count, and a marginal one unless an ancestor observes it.
 template <bool STATS>
@@ -81,7 +128,7 @@ __device__ __forceinline__ void node_anc_stage(const LevelParams &p, NodeWarp &Q
     }
     if (have) {
         const int x = (int)(key & 0xFFF), y = (int)((key >> 12) & 0xFFF);
-        const bool obs = observed<STATS>(HotDirect{p}, anc, na, x, y, z, st.anc, st.reads);
+        const bool obs = observed_fast<STATS>(p, anc, na, x, y, z, st.anc, st.reads);
         const int k0 = (int)(key >> 24);
         unsigned long long mask = mask0;
         while (mask) {
@@ -263,7 +310,8 @@ __device__ __forceinline__ void node_run(const LevelParams &p, const NodeSlice &
                 // the owner pixel (Eq. 5): from the float rows where their error bound decides it,
                 // else by the exact integer projection
                 int pu = 0, pv = 0;
-                int in = pixel_fast(fw, ex, ey, ez, rinf, p.W, p.H, pu, pv);
+                float zf_, ez_;
+                int in = pixel_fast(fw, ex, ey, ez, rinf, p.W, p.H, pu, pv, zf_, ez_);
                 if (in < 0) {
                     in = 0;
                     const int64_t Z = (int64_t)rw[8] * rxq + (int64_t)rw[9] * ryq + (int64_t)rw[10] * zq;

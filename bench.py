@@ -183,7 +183,7 @@ def profiled(kernel, workload):
     return out or None
 
 
-# Algorithmic bytes per unit of work (the survey's per-unit figures, applied to the units each
+# Algorithmic bytes per unit of work (the roofline's per-unit figures, applied to the units each
 # kernel processes): a voxel step or a brick jump reads 1 B; a cast ray reads its 16 B ray-table
 # entry and writes its 2 B step count; an enumerated voxel reads 1 B; a counted sample reads its
 # owner pixel's 2 B step count and 16 B ray entry; an ancestor test that reaches the buffer reads
@@ -201,7 +201,7 @@ def kernel_units(kernel, st):
 
 
 def method_bytes(st):
-    """The ray-by-ray method's own algorithmic bytes per evaluation (the survey's per-unit
+    """The ray-by-ray method's own algorithmic bytes per evaluation (the roofline's per-unit
     figures on the method's units: 1 B per DDA step of every ray, 4 B per ancestor depth read,
     4 B per rendered texel), counted by the instrumented pass."""
     return st["dda_steps"] + 4 * st["depth_reads"] + 4 * st["render_rays"]

@@ -107,6 +107,28 @@ def test_batch_wait_timeout_is_reported_and_recoverable(ctx):
             m.close()
 
 
+def test_batch_larger_than_one_launch(ctx):
+    """More trees than one persistent launch takes (they split into several launches) and more than
+    the trees it keeps in flight: every result equals its single evaluation."""
+    probs = [synth.random_small(900 + i, n_nodes=3 + i % 9, max_depth=1 + i % 4, sensor=Sensor(80, 55, 12, 9, 2.0, 4 + i % 5, 0.0))
+             for i in range(110)]
+    maps = [mig.Map(ctx, p.map.grid, p.map.voxel_size, p.map.origin) for p in probs[:10]]
+    tw, th, cps, eng0 = ctx.get_tiles()
+    ctx.set_tiles(tw, th, cps, 0)
+    try:
+        trees = [(p.tree.parent, p.tree.pos, p.sensor) for p in probs]
+        tmaps = [maps[i % 10] for i in range(len(probs))]
+        outs = mig.tree_eval_batch(ctx, trees, tmaps)
+        for i, (t, m, o) in enumerate(zip(trees, tmaps, outs)):
+            single = mig.tree_eval(m, *t)
+            for k in ("abs", "marg", "yaw"):
+                assert np.array_equal(o[k], single[k]), (i, k)
+    finally:
+        ctx.set_tiles(tw, th, cps, eng0)
+        for m in maps:
+            m.close()
+
+
 def test_batch_empty_and_invalid(ctx):
     assert mig.tree_eval_batch(ctx, [], []) == []
     p = synth.tiny()

@@ -166,8 +166,10 @@ def kernel_source_hash(kernel):
 
 def profiled(kernel, workload):
     """Figures of a committed ncu summary (profiles/<kernel>_<workload>.md) taken on the current
-    kernel source (the summary records the source hash): DRAM bytes per launch scaled to the
-    full launch, and the launch's own algorithmic units (for the scaling); else None."""
+    kernel source (the summary records the source hash), else None: DRAM bytes per launch over a
+    whole evaluation (a one-pass capture), and from a full capture of one launch its issue
+    activity, threads per instruction, L2 hit rate, L2-to-SM read rate (GB/s) and the bytes used
+    per 32-byte sector of its global loads."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -176,7 +178,8 @@ def profiled(kernel, workload):
     if not mh or mh.group(1) != kernel_source_hash(kernel):
         return None
     out = {}
-    for key in ("dram_bytes_per_launch", "issue_active_pct", "threads_per_inst", "l2_hit_pct"):
+    for key in ("dram_bytes_per_launch", "issue_active_pct", "threads_per_inst", "l2_hit_pct", "l2_to_sm_gbs",
+                "global_load_bytes_per_sector"):
         m = re.search(rf"{key}:\s*([0-9.eE+]+)", txt)
         if m:
             out[key] = float(m.group(1))
